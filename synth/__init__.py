@@ -1,0 +1,130 @@
+"""Seeded synthetic latency-series inputs shared by the oracle, the tests and the benchmark.
+
+The generator (``gen.c``) holds no arithmetic of the change-point method; it only draws
+series of uint32 cycle counts shaped like the size benchmarks' 2D result array (one row
+per array-size step, the first m latencies of each kept; paper Sec. IV-B-1, step (4)).
+Series are stored step-major, ``samples[offsets[s] + t*m_s + j]``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gen.c")
+_LIB = os.path.join(_HERE, "libmt4g_synth.so")
+MAX_CP = 8
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile gen.c into libmt4g_synth.so (plain gcc, no fast-math)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", "-o", tmp,
+                               _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        lib.mt4g_synth_params.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64,
+                                          i32p, i32p, i32p, i32p]
+        lib.mt4g_synth_params.restype = ctypes.c_int
+        lib.mt4g_synth_fill.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64,
+                                        ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p, ctypes.c_int]
+        lib.mt4g_synth_fill.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(ctypes.POINTER(t))
+
+
+@dataclass
+class Batch:
+    """A batch of series: step-major samples plus shapes and the generator's truth."""
+    samples: np.ndarray   # uint32 [offsets[-1]]
+    offsets: np.ndarray   # int64 [S+1]
+    steps: np.ndarray     # int32 [S]  (T_s)
+    m: np.ndarray         # int32 [S]
+    ncp: np.ndarray       # int32 [S]  true number of change points
+    cps: np.ndarray       # int32 [S, MAX_CP], -1 padded
+
+    @property
+    def S(self) -> int:
+        return int(self.steps.shape[0])
+
+    def series(self, s: int) -> np.ndarray:
+        """Series s as a [T, m] view."""
+        return self.samples[self.offsets[s]:self.offsets[s + 1]].reshape(int(self.steps[s]), int(self.m[s]))
+
+
+def params(cfg: int, seed: int, count: int, series_begin: int = 0):
+    lib = _load()
+    T = np.zeros(count, np.int32)
+    m = np.zeros(count, np.int32)
+    ncp = np.zeros(count, np.int32)
+    cps = np.zeros((count, MAX_CP), np.int32)
+    rc = lib.mt4g_synth_params(cfg, seed, series_begin, count, _ptr(T, ctypes.c_int32), _ptr(m, ctypes.c_int32),
+                               _ptr(ncp, ctypes.c_int32), _ptr(cps, ctypes.c_int32))
+    if rc != 0:
+        raise ValueError(f"unknown workload {cfg}")
+    return T, m, ncp, cps
+
+
+def generate(cfg: int, seed: int, count: int, series_begin: int = 0, nthreads: int | None = None,
+             out: np.ndarray | None = None) -> Batch:
+    """Generate series [series_begin, series_begin+count) of workload ``cfg``.
+
+    ``out`` may be a preallocated (e.g. pinned) uint32 array of at least the batch's size.
+    """
+    lib = _load()
+    T, m, ncp, cps = params(cfg, seed, count, series_begin)
+    offsets = np.zeros(count + 1, np.int64)
+    np.cumsum(T.astype(np.int64) * m.astype(np.int64), out=offsets[1:])
+    total = int(offsets[-1])
+    if out is None:
+        samples = np.empty(total, np.uint32)
+    else:
+        assert out.dtype == np.uint32 and out.size >= total
+        samples = out[:total]
+    if nthreads is None:
+        nthreads = os.cpu_count() or 1
+    rc = lib.mt4g_synth_fill(cfg, seed, series_begin, count, _ptr(offsets, ctypes.c_int64),
+                             samples.ctypes.data_as(ctypes.c_void_p), int(nthreads))
+    if rc != 0:
+        raise RuntimeError(f"mt4g_synth_fill failed ({rc})")
+    return Batch(samples, offsets, T, m, ncp, cps)
+
+
+def tiny_random(rng: np.random.Generator, S: int, T_range=(2, 8), m_range=(1, 4), vmax: int = 5) -> Batch:
+    """Small random series with heavy ties (values in 0..vmax) for exhaustive checks."""
+    T = rng.integers(T_range[0], T_range[1] + 1, size=S).astype(np.int32)
+    m = rng.integers(m_range[0], m_range[1] + 1, size=S).astype(np.int32)
+    offsets = np.zeros(S + 1, np.int64)
+    np.cumsum(T.astype(np.int64) * m, out=offsets[1:])
+    samples = rng.integers(0, vmax + 1, size=int(offsets[-1])).astype(np.uint32)
+    return Batch(samples, offsets, T, m, np.zeros(S, np.int32), -np.ones((S, MAX_CP), np.int32))
+
+
+def from_arrays(series_list) -> Batch:
+    """Pack a list of [T, m] uint32 arrays into one step-major batch."""
+    T = np.array([a.shape[0] for a in series_list], np.int32)
+    m = np.array([a.shape[1] for a in series_list], np.int32)
+    offsets = np.zeros(len(series_list) + 1, np.int64)
+    np.cumsum(T.astype(np.int64) * m, out=offsets[1:])
+    samples = np.concatenate([np.ascontiguousarray(a, dtype=np.uint32).ravel() for a in series_list]) \
+        if series_list else np.zeros(0, np.uint32)
+    S = len(series_list)
+    return Batch(samples, offsets, T, m, np.zeros(S, np.int32), -np.ones((S, MAX_CP), np.int32))
