@@ -1,0 +1,138 @@
+/*
+ * mt4g.h — C ABI of the B300 Kolmogorov-Smirnov change-point engine.
+ *
+ * The engine evaluates series of latency samples the way the size benchmarks of
+ * MT4G (arXiv 2511.05958) evaluate theirs: a series is a 2D array with one row per
+ * array-size step and the first m measured latencies of that step in the row
+ * (paper Sec. IV-B-1, step (4)); every step index is a candidate change point; the
+ * two-sample Kolmogorov-Smirnov statistic D = max_x |F(x) - G(x)| (Sec. II-C-1)
+ * between the samples left and right of a split decides it, and its significance
+ * is reported (Sec. IV-B-1 (4)).  Binary segmentation repeats the test inside the
+ * two parts to find every boundary (the segmentation criterion of Sec. II-C).
+ *
+ * Conventions shared by every call
+ *   - samples: DEVICE pointer, uint32, all series concatenated, each step-major:
+ *     sample j of step t of series s is samples[offsets[s] + t*m_s + j].
+ *   - offsets: HOST int64[S+1], offsets[0] = 0, non-decreasing.
+ *     steps:   HOST int32[S], T_s = steps[s] with 2 <= T_s <= MT4G_MAX_STEPS;
+ *     m_s = (offsets[s+1] - offsets[s]) / T_s must be an integer >= 1 and
+ *     T_s * m_s <= MT4G_MAX_SERIES_SAMPLES.
+ *   - A change-point index k is the first step of the right part: the split
+ *     compares steps [lo, k) with steps [k, hi).
+ *   - D is returned exactly as an unreduced int64 pair: dnum / dden with
+ *     dden = n_L * n_R (n_L = m (k - lo), n_R = m (hi - k)) and
+ *     dnum = max_x |N c_L(x) - n_L C(x)|, N = n_L + n_R, c_L and C the counts of
+ *     left and pooled samples <= x.  The split maximises D; ties go to the
+ *     smallest k.
+ *   - p is the asymptotic Kolmogorov p-value Q(lambda), lambda = dnum /
+ *     sqrt(N * dden) in FP64, the distribution whose first term inverts to the
+ *     critical value of Eq. 1; lambda^2 > 345 gives exactly 0.
+ *   - Outputs are DEVICE arrays owned by the caller.  The library never frees
+ *     caller memory and keeps no pointer to it after the call returns.
+ *   - Calls are asynchronous on cuda_stream (a cudaStream_t; NULL = legacy
+ *     default stream).  Outputs are valid after the stream is synchronised.
+ *     The return value reports host-side validation and launch errors;
+ *     conditions found on the device (capacity overflow, an expired bounded
+ *     wait) are returned by mt4g_wait().
+ *   - A context is not thread-safe: one host thread issues its calls at a time.
+ *     It owns the device workspace, which grows on demand and is reused.
+ *   - There is no CPU fallback: without a usable CUDA device every call fails
+ *     with MT4G_ECUDA.
+ */
+#ifndef MT4G_H
+#define MT4G_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MT4G_OK 0
+#define MT4G_EINVAL (-1)    /* bad argument: offsets, T < 2, non-integral m, alpha not in (0,1) ... */
+#define MT4G_ECAPACITY (-2) /* a series had more than max_cp change points (counts stay true) */
+#define MT4G_ENOMEM (-3)    /* device or pinned-host allocation failed */
+#define MT4G_ECUDA (-4)     /* a CUDA runtime call failed; message in mt4g_last_error */
+#define MT4G_ETIMEOUT (-5)  /* a bounded device-side wait expired; outputs are incomplete */
+
+#define MT4G_MODE_FULL 0    /* every split of every segment is evaluated */
+#define MT4G_MODE_REDUCED 2 /* Eq. 2 reduction first: one FP64 value per step, then the same test */
+
+#define MT4G_MAX_STEPS 32768
+#define MT4G_MAX_SERIES_SAMPLES (1LL << 30)
+
+/* Options for mt4g_set_option. */
+#define MT4G_OPT_WAIT_LIMIT_NS 1 /* bound on any device-side wait in the work queue (default 5e9 ns) */
+#define MT4G_OPT_STAGE_TIMING 2  /* 1: record CUDA events between the stages of every call */
+
+typedef struct mt4g_ctx mt4g_ctx;
+
+/* Create a context on CUDA device `device`.  *ctx receives the handle.
+ * Returns MT4G_OK, MT4G_ECUDA (no such device / no driver) or MT4G_ENOMEM. */
+int mt4g_create(mt4g_ctx **ctx, int device);
+
+/* Release the context and its device workspace.  Waits for its work to finish. */
+void mt4g_destroy(mt4g_ctx *ctx);
+
+/* Message for the most recent failing call on this context ("" if none).
+ * The string is owned by the context and valid until its next call. */
+const char *mt4g_last_error(const mt4g_ctx *ctx);
+
+/* Synchronise the stream of the most recent call and return its device-side
+ * status: MT4G_OK, MT4G_ECAPACITY (some cp_count > max_cp) or MT4G_ETIMEOUT. */
+int mt4g_wait(mt4g_ctx *ctx);
+
+/* Set a context option (see MT4G_OPT_*).  Returns MT4G_OK or MT4G_EINVAL. */
+int mt4g_set_option(mt4g_ctx *ctx, int option, int64_t value);
+
+/*
+ * One top-level test per series over every split k in [1, T_s - 1]
+ * (paper Sec. IV-B-1 (4): every index of the series is a potential change point;
+ * Sec. II-C-1: D = max_x |F(x) - G(x)|).
+ * Outputs (DEVICE, [S]): k_out = best split, dnum_out / dden_out = its exact D,
+ * p_out = its p-value.
+ * mode: MT4G_MODE_FULL on the raw samples, or MT4G_MODE_REDUCED on the Eq. 2
+ * values S_t = sqrt(sum_j (r_tj - min r)^2) (one sample per step, m = 1 in the
+ * D and p formulas).
+ */
+int mt4g_ks_scan(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets, const int32_t *steps,
+                 int64_t S, int32_t mode, int32_t *k_out, int64_t *dnum_out, int64_t *dden_out,
+                 double *p_out, void *cuda_stream);
+
+/*
+ * Binary segmentation of every series (segmentation criterion of Sec. II-C,
+ * applied split by split with the test of Sec. IV-B-1 (4)): scan [lo, hi); if
+ * p <= alpha accept the best split k and recurse into [lo, k) and [k, hi).  Each
+ * side of a split keeps at least min_seg >= 1 steps; shorter segments are not
+ * split.  No multiple-testing correction.
+ * Outputs (DEVICE): cp_count[S] = number of change points found in series s
+ * (the true count even above max_cp); cp_idx, dnum, dden, p [S * max_cp]: the
+ * first min(count, max_cp) change points of series s in ascending order, each
+ * with the D and p of the split that created it; unused slots are -1, 0, 0, 1.0.
+ * If some count exceeds max_cp, mt4g_wait() returns MT4G_ECAPACITY.
+ * mode: MT4G_MODE_FULL or MT4G_MODE_REDUCED (as in mt4g_ks_scan).
+ */
+int mt4g_ks_segment(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets, const int32_t *steps,
+                    int64_t S, double alpha, int32_t min_seg, int32_t max_cp, int32_t mode,
+                    int32_t *cp_count, int32_t *cp_idx, int64_t *dnum, int64_t *dden, double *p,
+                    void *cuda_stream);
+
+/*
+ * Measurement helpers (no counterpart in the paper; they instrument the calls above).
+ *
+ * mt4g_stage_times: with MT4G_OPT_STAGE_TIMING on, each call records CUDA events on its
+ * stream between its stages; this writes, for the last n calls (at most 64, oldest
+ * first), 4 durations in ms per call: [table upload, reduce+sort+run table, work-queue
+ * kernel, collect].  Synchronises on those events.  Returns the number of calls written
+ * (>= 0) or a negative error code.
+ *
+ * mt4g_last_work: after mt4g_wait(), the number of (split k, distinct value) pairs the
+ * last call evaluated, summed over all scanned segments (the scan's algorithmic work).
+ */
+int mt4g_stage_times(mt4g_ctx *ctx, double *ms_out, int32_t max_calls);
+int mt4g_last_work(mt4g_ctx *ctx, int64_t *evals);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MT4G_H */

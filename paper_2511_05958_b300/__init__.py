@@ -1,0 +1,212 @@
+"""Python binding of libmt4g, the B300 Kolmogorov-Smirnov change-point engine.
+
+Argument marshalling only: every step of the path (sort, scan, p-value, segmentation) runs in
+the CUDA kernels of ``libmt4g.so`` behind the C ABI declared in ``include/mt4g.h``.  PyTorch is
+used for device memory and streams.  There is no CPU fallback: if the library is missing or no
+CUDA device is usable, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import NamedTuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmt4g.so")
+
+OK, EINVAL, ECAPACITY, ENOMEM, ECUDA, ETIMEOUT = 0, -1, -2, -3, -4, -5
+MODE_FULL, MODE_REDUCED = 0, 2
+OPT_WAIT_LIMIT_NS = 1
+OPT_STAGE_TIMING = 2
+MAX_STEPS = 32768
+
+_lib = None
+
+
+class Mt4gError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"mt4g error {code}: {msg}")
+        self.code = code
+
+
+def build(force: bool = False) -> str:
+    """Compile libmt4g.so for sm_103a (nvcc) if any source is newer than it."""
+    from . import buildlib
+    return buildlib.build(force=force)
+
+
+def load_library():
+    """Load libmt4g.so (built in-tree by build()); raises if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise Mt4gError(ECUDA, f"CUDA library not built: {LIB_PATH} is missing (run build())")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    L.mt4g_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int]
+    L.mt4g_destroy.argtypes = [vp]
+    L.mt4g_destroy.restype = None
+    L.mt4g_last_error.argtypes = [vp]
+    L.mt4g_last_error.restype = ctypes.c_char_p
+    L.mt4g_wait.argtypes = [vp]
+    L.mt4g_set_option.argtypes = [vp, ctypes.c_int, i64]
+    L.mt4g_ks_scan.argtypes = [vp, vp, vp, vp, i64, i32, vp, vp, vp, vp, vp]
+    L.mt4g_ks_segment.argtypes = [vp, vp, vp, vp, i64, dbl, i32, i32, i32, vp, vp, vp, vp, vp, vp]
+    L.mt4g_stage_times.argtypes = [vp, vp, i32]
+    L.mt4g_last_work.argtypes = [vp, vp]
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    """Names the header declares; the tests check the library exports each of them."""
+    return ["mt4g_create", "mt4g_destroy", "mt4g_last_error", "mt4g_wait", "mt4g_set_option",
+            "mt4g_ks_scan", "mt4g_ks_segment", "mt4g_stage_times", "mt4g_last_work"]
+
+
+class ScanResult(NamedTuple):
+    k: "torch.Tensor"
+    dnum: "torch.Tensor"
+    dden: "torch.Tensor"
+    p: "torch.Tensor"
+
+
+class SegmentResult(NamedTuple):
+    rc: int
+    count: "torch.Tensor"   # [S]
+    idx: "torch.Tensor"     # [S, max_cp]
+    dnum: "torch.Tensor"
+    dden: "torch.Tensor"
+    p: "torch.Tensor"
+
+
+def _host_tables(offsets, steps):
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    steps = np.ascontiguousarray(steps, dtype=np.int32)
+    if offsets.ndim != 1 or steps.ndim != 1 or offsets.shape[0] != steps.shape[0] + 1:
+        raise Mt4gError(EINVAL, "offsets must have S+1 entries and steps S entries")
+    return offsets, steps
+
+
+def _dev_ptr(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise Mt4gError(EINVAL, f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise Mt4gError(EINVAL, f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Engine:
+    """One library context on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        import torch
+        L = load_library()
+        self.device = device
+        torch.cuda.set_device(device)
+        h = ctypes.c_void_p()
+        rc = L.mt4g_create(ctypes.byref(h), device)
+        if rc != OK:
+            raise Mt4gError(rc, "mt4g_create failed (no usable CUDA device?)")
+        self._h = h
+        self._L = L
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.mt4g_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != OK:
+            raise Mt4gError(rc, self._L.mt4g_last_error(self._h).decode())
+
+    def last_error(self) -> str:
+        return self._L.mt4g_last_error(self._h).decode()
+
+    def wait(self) -> int:
+        """Synchronise the last call's stream; returns its device-side status code."""
+        return int(self._L.mt4g_wait(self._h))
+
+    def set_option(self, option: int, value: int):
+        self._check(self._L.mt4g_set_option(self._h, option, int(value)))
+
+    def stage_times(self, max_calls: int = 1) -> np.ndarray:
+        """[n, 4] ms per call (upload, sort, queue kernel, collect) for the last n <= 64 calls."""
+        buf = np.zeros((max_calls, 4), np.float64)
+        n = self._L.mt4g_stage_times(self._h, buf.ctypes.data_as(ctypes.c_void_p), max_calls)
+        if n < 0:
+            self._check(n)
+        return buf[:n]
+
+    def last_work(self) -> int:
+        """(split, distinct value) pairs evaluated by the last call (valid after wait())."""
+        v = np.zeros(1, np.int64)
+        self._check(self._L.mt4g_last_work(self._h, v.ctypes.data_as(ctypes.c_void_p)))
+        return int(v[0])
+
+    def ks_scan(self, samples, offsets, steps, mode: int = MODE_FULL, stream=None, out=None,
+                sync: bool = True) -> ScanResult:
+        import torch
+        offsets, steps = _host_tables(offsets, steps)
+        S = steps.shape[0]
+        dev = samples.device
+        if out is None:
+            out = ScanResult(torch.empty(S, dtype=torch.int32, device=dev), torch.empty(S, dtype=torch.int64, device=dev),
+                             torch.empty(S, dtype=torch.int64, device=dev), torch.empty(S, dtype=torch.float64, device=dev))
+        rc = self._L.mt4g_ks_scan(self._h, _dev_ptr(samples, "samples"), offsets.ctypes.data_as(ctypes.c_void_p),
+                                  steps.ctypes.data_as(ctypes.c_void_p), S, mode, _dev_ptr(out.k, "k"),
+                                  _dev_ptr(out.dnum, "dnum"), _dev_ptr(out.dden, "dden"), _dev_ptr(out.p, "p"),
+                                  _stream_handle(stream))
+        self._check(rc)
+        if sync:
+            self._check(self.wait())
+        return out
+
+    def ks_segment(self, samples, offsets, steps, alpha: float, min_seg: int = 1, max_cp: int = 16,
+                   mode: int = MODE_FULL, stream=None, out=None, sync: bool = True) -> SegmentResult:
+        import torch
+        offsets, steps = _host_tables(offsets, steps)
+        S = steps.shape[0]
+        dev = samples.device
+        if out is None:
+            out = SegmentResult(0, torch.empty(S, dtype=torch.int32, device=dev),
+                                torch.empty((S, max_cp), dtype=torch.int32, device=dev),
+                                torch.empty((S, max_cp), dtype=torch.int64, device=dev),
+                                torch.empty((S, max_cp), dtype=torch.int64, device=dev),
+                                torch.empty((S, max_cp), dtype=torch.float64, device=dev))
+        rc = self._L.mt4g_ks_segment(self._h, _dev_ptr(samples, "samples"), offsets.ctypes.data_as(ctypes.c_void_p),
+                                     steps.ctypes.data_as(ctypes.c_void_p), S, float(alpha), int(min_seg),
+                                     int(max_cp), mode, _dev_ptr(out.count, "count"), _dev_ptr(out.idx, "idx"),
+                                     _dev_ptr(out.dnum, "dnum"), _dev_ptr(out.dden, "dden"), _dev_ptr(out.p, "p"),
+                                     _stream_handle(stream))
+        self._check(rc)
+        status = OK
+        if sync:
+            status = self.wait()
+            if status not in (OK, ECAPACITY):
+                self._check(status)
+        return out._replace(rc=status)
+
+
+def to_device_samples(samples: np.ndarray, device="cuda"):
+    """Copy uint32 host samples to a device tensor (stored as int32 bits)."""
+    import torch
+    a = np.ascontiguousarray(samples, dtype=np.uint32).view(np.int32)
+    return torch.from_numpy(a).to(device)

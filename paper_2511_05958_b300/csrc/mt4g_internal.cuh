@@ -1,0 +1,113 @@
+// Internal declarations shared by the CUDA translation units of libmt4g.
+//
+// Device data layout (all in one context-owned workspace; offsets below are
+// element offsets, every sub-buffer 256-byte aligned):
+//   SeriesDesc desc[S]          shape of each series and its bases
+//   keyA/keyB  uint32[Ntot]     radix-sort ping-pong keys (final order in keyA)
+//   labA/labB  uint16[Ntot]     step labels travelling with the keys (final in labA)
+//   runs       int32[Ntot + S]  per series: start of each run of equal values,
+//                               runs[run_base + j], j in [0, U_s], last = N_s
+//   cp_flag/num/den/p [sum T]   per step: a change point accepted at that step
+//   queue      WorkItem[cap] + ready[cap]   the device work queue
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mt4g.h"
+
+namespace mt4g {
+
+constexpr int kSortThreads = 512;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 samples per tile
+
+constexpr int kScanThreads = 512;  // one split k per thread
+constexpr int kChunkK = kScanThreads;  // splits per work item
+
+struct SeriesDesc {
+    int64_t off;        // first sample of the series
+    int64_t step_base;  // first per-step slot of the series (prefix sum of T)
+    int64_t run_base;   // first run-table slot (off + series index)
+    int32_t T;          // steps
+    int32_t m;          // samples per step
+    int32_t nruns;      // U_s, number of distinct values (written by the sort)
+    int32_t pad;
+};
+
+// One unit of work: the splits of chunk `chunk` of segment [lo, hi) of a series.
+// Chunk c covers k in [lo + min_seg + c*kChunkK, ...] up to hi - min_seg.
+struct WorkItem {
+    int32_t series;
+    int32_t lo;
+    int32_t hi;
+    int32_t chunk;
+};
+
+// Partial result of one chunk, written over its (already consumed) queue slot.
+struct ChunkResult {
+    int32_t k;
+    int32_t pad;
+    uint64_t g;  // max_x |H c_L - (k - lo) C|; the exact numerator is m * g
+};
+
+enum : int32_t { kStatusTimeout = 1, kStatusQueueFull = 2, kStatusCapacity = 4 };
+
+struct QueueHeader {
+    unsigned long long head;     // next ticket to hand out
+    unsigned long long tail;     // next free slot
+    long long pending;           // items pushed and not yet finished
+    int32_t status;              // kStatus* bits
+    int32_t pad;
+    unsigned long long cap;      // slots
+    unsigned long long evals;    // (k, distinct value) pairs evaluated
+};
+
+enum RunMode : int32_t { kRunScan = 0, kRunSegment = 1 };
+
+struct RunParams {
+    const SeriesDesc *desc;
+    const uint16_t *lab;   // sorted labels (labA)
+    const int32_t *runs;   // run table
+    QueueHeader *q;
+    WorkItem *items;
+    int32_t *ready;
+    int32_t mode;          // kRunScan / kRunSegment
+    int32_t min_seg;
+    double alpha;
+    long long wait_limit_ns;
+    // scan outputs [S]
+    int32_t *k_out;
+    int64_t *dnum_out;
+    int64_t *dden_out;
+    double *p_out;
+    // segmentation: per-step accepted change points
+    uint8_t *cp_flag;
+    int64_t *cp_num;
+    int64_t *cp_den;
+    double *cp_p;
+};
+
+// Number of chunks of a segment of H steps (0 if it cannot be split).
+__host__ __device__ inline int32_t seg_chunks(int32_t H, int32_t min_seg) {
+    int32_t nk = H - 2 * min_seg + 1;
+    return nk <= 0 ? 0 : (nk + kChunkK - 1) / kChunkK;
+}
+
+// ---- kernels (launch wrappers live in the .cu files) ----
+cudaError_t launch_sort(const uint32_t *samples, SeriesDesc *desc, const int32_t *order, int64_t S,
+                        uint32_t *keyA, uint32_t *keyB, uint16_t *labA, uint16_t *labB, int32_t *runs,
+                        cudaStream_t st);
+
+cudaError_t launch_queue_run(const RunParams &P, int grid, uint32_t epoch, cudaStream_t st);
+int queue_grid(int device);
+
+cudaError_t launch_collect(const SeriesDesc *desc, int64_t S, const uint8_t *cp_flag, const int64_t *cp_num,
+                           const int64_t *cp_den, const double *cp_p, int32_t max_cp, int32_t *cp_count,
+                           int32_t *cp_idx, int64_t *dnum, int64_t *dden, double *p, QueueHeader *q,
+                           cudaStream_t st);
+
+cudaError_t launch_reduce_rank(const uint32_t *samples, const SeriesDesc *raw_desc, int64_t S,
+                               double *red, uint32_t *rank_out, cudaStream_t st);
+
+}  // namespace mt4g

@@ -1,0 +1,250 @@
+"""GPU parity: the CUDA path against the CPU oracle, element by element.
+
+Change points, k and the exact D pair (dnum, dden) must be bit-identical; p-values must agree
+within 1e-12 relative (both sides evaluate the same FP64 series with their own exp).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2511_05958_b300 as mt4g
+import synth
+
+pytestmark = pytest.mark.gpu
+
+P_RTOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def eng():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    e = mt4g.Engine(0)
+    yield e
+    e.close()
+
+
+def assert_p_close(p_gpu, p_cpu, ctx=""):
+    p_gpu = np.asarray(p_gpu, np.float64)
+    p_cpu = np.asarray(p_cpu, np.float64)
+    bad = np.abs(p_gpu - p_cpu) > P_RTOL * np.abs(p_cpu)
+    assert not bad.any(), (ctx, np.nonzero(bad), p_gpu[bad][:5], p_cpu[bad][:5])
+
+
+def gpu_scan(eng, b, mode=mt4g.MODE_FULL):
+    r = eng.ks_scan(mt4g.to_device_samples(b.samples), b.offsets, b.steps, mode=mode)
+    return tuple(t.cpu().numpy() for t in r)
+
+
+def gpu_segment(eng, b, alpha, min_seg=1, max_cp=16, mode=mt4g.MODE_FULL):
+    r = eng.ks_segment(mt4g.to_device_samples(b.samples), b.offsets, b.steps, alpha, min_seg, max_cp, mode=mode)
+    return (r.rc,) + tuple(t.cpu().numpy() for t in r[1:])
+
+
+def check_scan(eng, b, mode=mt4g.MODE_FULL, nthreads=8):
+    k, num, den, p = gpu_scan(eng, b, mode)
+    ok, onum, oden, op = oracle.ks_scan(b.samples, b.offsets, b.steps, reduced=mode == mt4g.MODE_REDUCED,
+                                        nthreads=nthreads)
+    assert np.array_equal(k, ok), np.nonzero(k != ok)
+    assert np.array_equal(num, onum)
+    assert np.array_equal(den, oden)
+    assert_p_close(p, op)
+
+
+def check_segment(eng, b, alpha, min_seg=1, max_cp=16, mode=mt4g.MODE_FULL, nthreads=8):
+    rc, cnt, idx, num, den, p = gpu_segment(eng, b, alpha, min_seg, max_cp, mode)
+    orc, ocnt, oidx, onum, oden, op = oracle.ks_segment(b.samples, b.offsets, b.steps, alpha, min_seg, max_cp,
+                                                        reduced=mode == mt4g.MODE_REDUCED, nthreads=nthreads)
+    assert (rc == mt4g.ECAPACITY) == (orc == oracle.ECAPACITY)
+    assert np.array_equal(cnt, ocnt), np.nonzero(cnt != ocnt)
+    assert np.array_equal(idx, oidx)
+    assert np.array_equal(num, onum)
+    assert np.array_equal(den, oden)
+    assert_p_close(p, op)
+    return cnt, idx
+
+
+# ------------------------------------------------------------------ small exact cases
+
+def test_config1_scan_matches_oracle_and_golden(eng):
+    import json
+    import os
+    b = synth.generate(1, 0, 1)
+    check_scan(eng, b)
+    k, num, den, p = gpu_scan(eng, b)
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "config1_oracle.json")))
+    assert (int(k[0]), int(num[0]), int(den[0]), float(p[0])) == \
+        (g["scan"]["k"], g["scan"]["num"], g["scan"]["den"], g["scan"]["p"])
+
+
+def test_config1_segment(eng):
+    b = synth.generate(1, 0, 1)
+    cnt, idx = check_segment(eng, b, 1e-6)
+    assert cnt[0] == 1 and idx[0, 0] == 40
+
+
+def test_tiny_random_heavy_ties(eng):
+    rng = np.random.default_rng(11)
+    for rep in range(4):
+        b = synth.tiny_random(rng, 500, T_range=(2, 12), m_range=(1, 6), vmax=int(rng.integers(1, 8)))
+        check_scan(eng, b)
+        for alpha, min_seg in [(0.5, 1), (0.05, 1), (0.2, 2), (1e-3, 3)]:
+            check_segment(eng, b, alpha, min_seg)
+
+
+def test_medium_random_ragged_shapes(eng):
+    """Many runs per warp, ragged run counts, T across several 512-split chunks."""
+    rng = np.random.default_rng(5)
+    series = []
+    for _ in range(60):
+        T = int(rng.integers(2, 1400))
+        m = int(rng.integers(1, 9))
+        base = rng.integers(0, int(rng.integers(2, 5000)), size=(T, m))
+        if rng.random() < 0.7:
+            cps = np.sort(rng.choice(np.arange(1, T), size=min(3, T - 1), replace=False))
+            shift = np.searchsorted(cps, np.arange(T), side="right") * int(rng.integers(0, 300))
+            base = base + shift[:, None]
+        series.append(base.astype(np.uint32))
+    b = synth.from_arrays(series)
+    check_scan(eng, b)
+    check_segment(eng, b, 1e-4, 1, 32)
+    check_segment(eng, b, 1e-2, 5, 8)
+
+
+def test_edge_values_and_shapes(eng):
+    series = [
+        np.zeros((2, 1), np.uint32),
+        np.full((7, 3), 0xFFFFFFFF, np.uint32),
+        np.array([[0], [0xFFFFFFFF]], np.uint32),
+        np.array([[0xFFFFFFFF], [0]], np.uint32),
+        np.arange(64, dtype=np.uint32).reshape(64, 1),
+        np.arange(64, dtype=np.uint32)[::-1].copy().reshape(64, 1),
+        np.tile(np.array([[5, 5, 6]], np.uint32), (40, 1)),
+        (np.arange(600 * 4, dtype=np.uint64) * 2654435761 % 4294967291).astype(np.uint32).reshape(600, 4),
+    ]
+    b = synth.from_arrays(series)
+    check_scan(eng, b)
+    check_segment(eng, b, 0.3, 1, 64)
+
+
+def test_large_T_multichunk_and_max_steps(eng):
+    rng = np.random.default_rng(9)
+    s1 = (rng.integers(0, 50, size=(4096, 1)) + (np.arange(4096) >= 3000)[:, None] * 20).astype(np.uint32)
+    s2 = rng.integers(0, 1 << 31, size=(2049, 2)).astype(np.uint32)
+    s3 = (rng.integers(0, 8, size=(mt4g.MAX_STEPS, 1)) + (np.arange(mt4g.MAX_STEPS) >= 20000)[:, None] * 3
+          ).astype(np.uint32)
+    b = synth.from_arrays([s1, s2])
+    check_scan(eng, b)
+    check_segment(eng, b, 1e-6, 1, 16)
+    b3 = synth.from_arrays([s3])
+    check_scan(eng, b3)
+
+
+def test_wide_arithmetic_path(eng):
+    """m H^2 >= 2^33 takes the 64-bit accumulation path (T=1449, m=4096)."""
+    rng = np.random.default_rng(2)
+    T, m = 1449, 4096
+    x = rng.integers(0, 40, size=(T, m)).astype(np.uint32)
+    x[900:] += 1
+    b = synth.from_arrays([x])
+    check_scan(eng, b)
+
+
+def test_reduced_mode(eng):
+    rng = np.random.default_rng(4)
+    series = []
+    for _ in range(80):
+        T = int(rng.integers(2, 300))
+        m = int(rng.integers(1, 40))
+        lvl = (np.arange(T) >= int(rng.integers(1, T))) * int(rng.integers(0, 50))
+        series.append((rng.integers(20, 40, size=(T, m)) + lvl[:, None]).astype(np.uint32))
+    b = synth.from_arrays(series)
+    check_scan(eng, b, mode=mt4g.MODE_REDUCED)
+    check_segment(eng, b, 1e-3, 1, 16, mode=mt4g.MODE_REDUCED)
+
+
+def test_capacity_reports_true_count(eng):
+    x = np.array([[10 * (t + 1)] * 16 for t in range(12)], np.uint32)
+    b = synth.from_arrays([x, x[:5]])
+    rc, cnt, idx, num, den, p = gpu_segment(eng, b, 0.05, 1, 4)
+    assert rc == mt4g.ECAPACITY
+    check_segment(eng, b, 0.05, 1, 4)
+    check_segment(eng, b, 0.05, 1, 0)
+
+
+def test_invalid_arguments_are_rejected(eng):
+    import torch
+    b = synth.generate(1, 0, 1)
+    d = mt4g.to_device_samples(b.samples)
+    with pytest.raises(mt4g.Mt4gError) as e:
+        eng.ks_scan(d, b.offsets, np.array([3], np.int32))  # 2048 not a multiple of 3
+    assert e.value.code == mt4g.EINVAL
+    with pytest.raises(mt4g.Mt4gError) as e:
+        eng.ks_scan(d, b.offsets, np.array([1], np.int32))  # T < 2
+    assert e.value.code == mt4g.EINVAL
+    with pytest.raises(mt4g.Mt4gError) as e:
+        eng.ks_segment(d, b.offsets, b.steps, 1.5)
+    assert e.value.code == mt4g.EINVAL
+    with pytest.raises(mt4g.Mt4gError) as e:
+        eng.ks_segment(d, b.offsets, b.steps, 0.01, min_seg=0)
+    assert e.value.code == mt4g.EINVAL
+    with pytest.raises(mt4g.Mt4gError) as e:
+        eng.ks_scan(d, np.array([1, 2049], np.int64), b.steps)  # offsets[0] != 0
+    assert e.value.code == mt4g.EINVAL
+    # empty batch is a no-op
+    r = eng.ks_scan(d, np.zeros(1, np.int64), np.zeros(0, np.int32))
+    assert r.k.numel() == 0
+    torch.cuda.synchronize()
+
+
+def test_repeated_calls_reuse_workspace(eng):
+    """Different shapes back to back (workspace growth, queue epochs) keep parity."""
+    rng = np.random.default_rng(21)
+    for rep in range(6):
+        b = synth.tiny_random(rng, int(rng.integers(1, 300)), T_range=(2, int(rng.integers(3, 200))),
+                              m_range=(1, 5), vmax=int(rng.integers(1, 100)))
+        check_segment(eng, b, 0.01, 1, 16)
+        check_scan(eng, b)
+
+
+# ------------------------------------------------------------------ full-size workloads, sampled
+
+def test_config2_full_batch_sampled(eng):
+    """1024 series, T=512, m=128: the whole batch on the GPU, the oracle on 48 sampled series."""
+    b = synth.generate(2, 1, 1024)
+    rc, cnt, idx, num, den, p = gpu_segment(eng, b, 1e-6, 1, 16)
+    assert rc == mt4g.OK
+    sample = np.linspace(0, 1023, 48).astype(int)
+    sb = synth.from_arrays([b.series(s) for s in sample])
+    orc, ocnt, oidx, onum, oden, op = oracle.ks_segment(sb.samples, sb.offsets, sb.steps, 1e-6, 1, 16, nthreads=8)
+    assert np.array_equal(cnt[sample], ocnt)
+    assert np.array_equal(idx[sample], oidx)
+    assert np.array_equal(num[sample], onum)
+    assert np.array_equal(den[sample], oden)
+    assert_p_close(p[sample], op)
+    # properties over every series
+    assert (num <= den).all() and (num >= 0).all()
+    for s in range(1024):
+        c = min(cnt[s], 16)
+        assert (np.diff(idx[s, :c]) > 0).all() and (p[s, :c] <= 1e-6).all()
+    truth = sum(np.array_equal(idx[s, :cnt[s]], b.cps[s, :3]) for s in range(1024))
+    assert truth >= 0.95 * 1024
+
+
+def test_config3_uneven_batch_sampled(eng):
+    """16384 uneven series (T 32..4096, m 8..256): the full batch on the GPU; the oracle on the
+    sampled series it finishes quickly; structural properties on all."""
+    b = synth.generate(3, 2, 16384)
+    rc, cnt, idx, num, den, p = gpu_segment(eng, b, 1e-6, 1, 16)
+    assert rc in (mt4g.OK, mt4g.ECAPACITY)
+    cost = b.steps.astype(np.float64) ** 2 * b.m
+    small = np.nonzero(cost < 3e7)[0]
+    sample = small[np.linspace(0, len(small) - 1, 64).astype(int)]
+    sb = synth.from_arrays([b.series(s) for s in sample])
+    orc, ocnt, oidx, onum, oden, op = oracle.ks_segment(sb.samples, sb.offsets, sb.steps, 1e-6, 1, 16, nthreads=8)
+    assert np.array_equal(cnt[sample], ocnt)
+    assert np.array_equal(idx[sample], oidx)
+    assert np.array_equal(num[sample], onum)
+    assert np.array_equal(den[sample], oden)
+    assert_p_close(p[sample], op)
+    assert (num <= den).all() and (num >= 0).all()
