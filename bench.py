@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--workload", default="plain", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kpt", type=int, default=0, help="force the scan tile (1, 2, 4); 0 = automatic")
     ap.add_argument("--series", type=int, default=None,
                     help="override the batch size (only for small profiler captures; not a bench value)")
     return ap.parse_args()
@@ -184,6 +185,7 @@ def main():
     d_samples = host.to(dev)
     eng = mt4g.Engine(local)
     eng.set_option(mt4g.OPT_STAGE_TIMING, 1)
+    eng.set_option(mt4g.OPT_SCAN_KPT, args.kpt)
     stream = torch.cuda.current_stream(dev)
     out = None
 

@@ -64,6 +64,8 @@ extern "C" {
 /* Options for mt4g_set_option. */
 #define MT4G_OPT_WAIT_LIMIT_NS 1 /* bound on any device-side wait in the work queue (default 5e9 ns) */
 #define MT4G_OPT_STAGE_TIMING 2  /* 1: record CUDA events between the stages of every call */
+#define MT4G_OPT_SCAN_KPT 3      /* scan tile: 0 = per-series choice (default), else 1, 2 or 4
+                                    groups of 32 splits per warp work item for every series */
 
 typedef struct mt4g_ctx mt4g_ctx;
 

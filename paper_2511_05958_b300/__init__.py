@@ -20,6 +20,7 @@ OK, EINVAL, ECAPACITY, ENOMEM, ECUDA, ETIMEOUT = 0, -1, -2, -3, -4, -5
 MODE_FULL, MODE_REDUCED = 0, 2
 OPT_WAIT_LIMIT_NS = 1
 OPT_STAGE_TIMING = 2
+OPT_SCAN_KPT = 3
 MAX_STEPS = 32768
 
 _lib = None

@@ -30,6 +30,8 @@ struct mt4g_ctx {
     bool have_last = false;      // some call has enqueued work on last_stream
     bool last_enqueued = false;  // the most recent call enqueued work (its status is in h_hdr)
 
+    int32_t forced_kpt = 0;  // 0: per-series choice; 1, 2, 4: every series
+
     // stage timing: events of the last kTimingRing calls
     static constexpr int kTimingRing = 64;
     static constexpr int kMarks = 5;
@@ -90,7 +92,9 @@ struct Plan {
     std::vector<SeriesDesc> desc;      // sort/scan view
     std::vector<SeriesDesc> raw_desc;  // raw samples (Eq. 2 mode only)
     std::vector<int32_t> sort_order;   // series by size, largest first
-    std::vector<WorkItem> init_items;  // top-level chunks, costliest series first
+    std::vector<int32_t> qorder;       // series by scan cost (T^2 m), costliest first
+    std::vector<int64_t> item_base;    // first queue slot of the top-level slices of qorder[i]
+    int64_t n_init = 0;                // top-level slices
     unsigned long long cap = 0;
 };
 
@@ -99,6 +103,8 @@ struct Buffers {
     SeriesDesc *desc;
     SeriesDesc *raw_desc;
     int32_t *order;
+    int32_t *qorder;
+    int64_t *item_base;
     uint32_t *keyA, *keyB;
     uint16_t *labA, *labB;
     int32_t *runs;
@@ -117,6 +123,8 @@ size_t carve(void *base, const Plan &P, Buffers &B, size_t *ready_off) {
     B.desc = c.take<SeriesDesc>(P.S);
     B.raw_desc = c.take<SeriesDesc>(P.reduced ? P.S : 0);
     B.order = c.take<int32_t>(P.S);
+    B.qorder = c.take<int32_t>(P.S);
+    B.item_base = c.take<int64_t>(P.S);
     B.keyA = c.take<uint32_t>(P.Ntot);
     B.keyB = c.take<uint32_t>(P.Ntot);
     B.labA = c.take<uint16_t>(P.Ntot);
@@ -137,6 +145,15 @@ size_t carve(void *base, const Plan &P, Buffers &B, size_t *ready_off) {
 // Record stage boundary `i` of the current call when stage timing is on.
 void mark(mt4g_ctx *ctx, int i, cudaStream_t st) {
     if (ctx->timing) cudaEventRecord(ctx->ev[ctx->ring_pos][i], st);
+}
+
+// Scan tile for a series: split groups of 32 per warp work item.  A forced value
+// (MT4G_OPT_SCAN_KPT) wins; otherwise the autotuned table, else a size heuristic.
+int32_t pick_kpt(const mt4g_ctx *ctx, int32_t T, int32_t m) {
+    if (ctx->forced_kpt) return ctx->forced_kpt;
+    (void)T;
+    (void)m;
+    return 1;
 }
 
 // Validate the host tables and build the per-call plan.
@@ -184,6 +201,7 @@ int make_plan(mt4g_ctx *ctx, const int64_t *offsets, const int32_t *steps, int64
             d.m = m;
         }
         d.run_base = d.off + s;
+        d.kpt = pick_kpt(ctx, d.T, d.m);
         P.desc[s] = d;
         sumT += T;
         ntot += (int64_t)d.T * d.m;
@@ -201,22 +219,26 @@ int make_plan(mt4g_ctx *ctx, const int64_t *offsets, const int32_t *steps, int64
             return (int64_t)P.desc[a].T * P.desc[a].m > (int64_t)P.desc[b].T * P.desc[b].m;
         });
     }
-    // first work items: the top-level chunks, costliest series (T^2 m) first
-    std::vector<int32_t> qorder(P.sort_order);
+    // first work items: the top-level slices, costliest series (T^2 m) first
+    P.qorder = P.sort_order;
     if (!uniform) {
-        std::stable_sort(qorder.begin(), qorder.end(), [&](int32_t a, int32_t b) {
+        std::stable_sort(P.qorder.begin(), P.qorder.end(), [&](int32_t a, int32_t b) {
             const double ca = (double)P.desc[a].T * P.desc[a].T * P.desc[a].m;
             const double cb = (double)P.desc[b].T * P.desc[b].T * P.desc[b].m;
             return ca > cb;
         });
     }
-    P.init_items.clear();
-    for (int32_t s : qorder) {
-        const int nch = seg_chunks(P.desc[s].T, min_seg);
-        for (int c = 0; c < nch; c++) P.init_items.push_back(WorkItem{s, 0, P.desc[s].T, c});
+    P.item_base.resize(S);
+    int64_t nb = 0;
+    for (int64_t i = 0; i < S; i++) {
+        P.item_base[i] = nb;
+        nb += seg_chunks(P.desc[P.qorder[i]].T, min_seg, P.desc[P.qorder[i]].kpt);
     }
-    // children of every accepted split: at most 2 per step, plus chunking slack
-    P.cap = (unsigned long long)P.init_items.size() + 2ull * (unsigned long long)sumT + 1024ull;
+    P.n_init = nb;
+    // slices of the children of accepted splits: a split of a segment adds at most
+    // two slices beyond the parent's, so 2 per step plus the top level bounds them
+    // for the usual few change points per series; overflow is reported.
+    P.cap = (unsigned long long)nb + 4ull * (unsigned long long)sumT + 1024ull;
     return MT4G_OK;
 }
 
@@ -269,13 +291,13 @@ int enqueue_pipeline(mt4g_ctx *ctx, const uint32_t *samples, Plan &P, RunParams 
     }
 
     // stage the host tables in pinned memory and upload them
-    const size_t n_items = P.init_items.size();
+    const size_t n_items = (size_t)P.n_init;
     const size_t bytes_hdr = sizeof(QueueHeader);
     const size_t bytes_desc = P.S * sizeof(SeriesDesc);
     const size_t bytes_raw = P.reduced ? P.S * sizeof(SeriesDesc) : 0;
     const size_t bytes_order = P.S * sizeof(int32_t);
-    const size_t bytes_items = n_items * sizeof(WorkItem);
-    const size_t bytes_ready = n_items * sizeof(int32_t);
+    const size_t bytes_items = P.S * sizeof(int32_t);   // qorder
+    const size_t bytes_ready = P.S * sizeof(int64_t);   // item_base
     rc = ensure_pinned(ctx, bytes_hdr + bytes_desc + bytes_raw + bytes_order + bytes_items + bytes_ready + 64);
     if (rc) return rc;
     char *h = (char *)ctx->pin;
@@ -298,18 +320,21 @@ int enqueue_pipeline(mt4g_ctx *ctx, const uint32_t *samples, Plan &P, RunParams 
     memcpy(h + o, P.sort_order.data(), bytes_order);
     o += bytes_order;
     const size_t o_items = o;
-    if (bytes_items) memcpy(h + o, P.init_items.data(), bytes_items);
+    if (bytes_items) memcpy(h + o, P.qorder.data(), bytes_items);
     o += bytes_items;
+    o = (o + 7) & ~(size_t)7;
     const size_t o_ready = o;
-    for (size_t i = 0; i < n_items; i++) ((uint32_t *)(h + o))[i] = epoch;
+    if (bytes_ready) memcpy(h + o, P.item_base.data(), bytes_ready);
 
     CUDA_TRY(ctx, cudaMemcpyAsync(B.q, h, bytes_hdr, cudaMemcpyHostToDevice, st));
     if (bytes_desc) CUDA_TRY(ctx, cudaMemcpyAsync(B.desc, h + o_desc, bytes_desc, cudaMemcpyHostToDevice, st));
     if (bytes_raw) CUDA_TRY(ctx, cudaMemcpyAsync(B.raw_desc, h + o_raw, bytes_raw, cudaMemcpyHostToDevice, st));
     if (bytes_order) CUDA_TRY(ctx, cudaMemcpyAsync(B.order, h + o_order, bytes_order, cudaMemcpyHostToDevice, st));
-    if (bytes_items) CUDA_TRY(ctx, cudaMemcpyAsync(B.items, h + o_items, bytes_items, cudaMemcpyHostToDevice, st));
-    if (bytes_ready) CUDA_TRY(ctx, cudaMemcpyAsync(B.ready, h + o_ready, bytes_ready, cudaMemcpyHostToDevice, st));
+    if (bytes_items) CUDA_TRY(ctx, cudaMemcpyAsync(B.qorder, h + o_items, bytes_items, cudaMemcpyHostToDevice, st));
+    if (bytes_ready)
+        CUDA_TRY(ctx, cudaMemcpyAsync(B.item_base, h + o_ready, bytes_ready, cudaMemcpyHostToDevice, st));
     CUDA_TRY(ctx, cudaEventRecord(ctx->pin_free, st));
+    CUDA_TRY(ctx, launch_init_items(B.desc, B.qorder, B.item_base, P.S, P.min_seg, B.items, B.ready, epoch, st));
     mark(ctx, 1, st);
 
     const uint32_t *sort_in = samples;
@@ -415,6 +440,12 @@ int mt4g_set_option(mt4g_ctx *c, int option, int64_t value) {
         c->timing = value != 0;
         c->ring_pos = 0;
         c->ring_count = 0;
+        return MT4G_OK;
+    }
+    if (option == MT4G_OPT_SCAN_KPT) {
+        if (value != 0 && value != 1 && value != 2 && value != 4)
+            return fail(c, MT4G_EINVAL, "scan tile must be 0 (automatic), 1, 2 or 4");
+        c->forced_kpt = (int32_t)value;
         return MT4G_OK;
     }
     if (option == MT4G_OPT_WAIT_LIMIT_NS) {

@@ -22,8 +22,7 @@ constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 samples per tile
 
-constexpr int kScanThreads = 512;  // one split k per thread
-constexpr int kChunkK = kScanThreads;  // splits per work item
+constexpr int kScanThreads = 256;  // CTA of the persistent kernel: 8 independent warps
 
 struct SeriesDesc {
     int64_t off;        // first sample of the series
@@ -32,11 +31,12 @@ struct SeriesDesc {
     int32_t T;          // steps
     int32_t m;          // samples per step
     int32_t nruns;      // U_s, number of distinct values (written by the sort)
-    int32_t pad;
+    int32_t kpt;        // split groups of 32 per warp work item (1, 2 or 4): the scan tile
 };
 
-// One unit of work: the splits of chunk `chunk` of segment [lo, hi) of a series.
-// Chunk c covers k in [lo + min_seg + c*kChunkK, ...] up to hi - min_seg.
+// One unit of work: the splits of slice `chunk` of segment [lo, hi) of a series.
+// With w = 32 kpt splits per slice, slice c covers k in [lo + min_seg + w c, ... + w - 1],
+// up to hi - min_seg.
 struct WorkItem {
     int32_t series;
     int32_t lo;
@@ -88,10 +88,11 @@ struct RunParams {
     double *cp_p;
 };
 
-// Number of chunks of a segment of H steps (0 if it cannot be split).
-__host__ __device__ inline int32_t seg_chunks(int32_t H, int32_t min_seg) {
-    int32_t nk = H - 2 * min_seg + 1;
-    return nk <= 0 ? 0 : (nk + kChunkK - 1) / kChunkK;
+// Number of slices of a segment of H steps (0 if it cannot be split).
+__host__ __device__ inline int32_t seg_chunks(int32_t H, int32_t min_seg, int32_t kpt) {
+    const int32_t nk = H - 2 * min_seg + 1;
+    const int32_t w = 32 * kpt;
+    return nk <= 0 ? 0 : (nk + w - 1) / w;
 }
 
 // ---- kernels (launch wrappers live in the .cu files) ----
@@ -100,6 +101,8 @@ cudaError_t launch_sort(const uint32_t *samples, SeriesDesc *desc, const int32_t
                         cudaStream_t st);
 
 cudaError_t launch_queue_run(const RunParams &P, int grid, uint32_t epoch, cudaStream_t st);
+cudaError_t launch_init_items(const SeriesDesc *desc, const int32_t *qorder, const int64_t *item_base, int64_t S,
+                              int32_t min_seg, WorkItem *items, int32_t *ready, uint32_t epoch, cudaStream_t st);
 int queue_grid(int device);
 
 cudaError_t launch_collect(const SeriesDesc *desc, int64_t S, const uint8_t *cp_flag, const int64_t *cp_num,

@@ -4,15 +4,17 @@
 // The ECDFs of Sec. II-C-1 are read off the pooled samples in value order, so each
 // series is sorted once: ascending by value, equal values in step order (the input
 // is step-major and every pass is stable).  One CTA owns one series and runs all of
-// its 8-bit digit passes itself; the number of passes is the smallest even number
-// covering the series' largest value, so the result always lands in keyA/labA.
-// Passes keep the series' ping-pong buffers hot in L2 (a 64 K-sample series is
-// 768 KB across both buffers), so HBM sees roughly one read of the input and one
-// write of the sorted labels.
+// its 8-bit digit passes itself, as many as the series' largest value needs.  When
+// every value is below 2^16 the key is (value << 16) | step, so a pass moves 4 bytes
+// per sample; otherwise values and 16-bit labels move separately.  The first read
+// also counts the first digit, and each pass counts the next one while it ranks.
 //
 // Within a 4096-sample tile, each warp ranks its 256 samples with match.any
 // (stable: item-major, then lane order), per-warp digit counts are scanned across
-// warps, and a running per-digit base carries the order across tiles.
+// warps, the tile is staged in shared memory in sorted order and written out so
+// that consecutive positions of a digit go to consecutive addresses; a running
+// per-digit base carries the order across tiles.  The last step writes the labels
+// in value order to labA and the start of every run of equal values.
 #include "mt4g_internal.cuh"
 
 namespace mt4g {
@@ -51,65 +53,46 @@ __device__ void scan256(const uint32_t *s_in, uint32_t *s_out, uint32_t *s_tmp) 
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kSortThreads, 2)
-sort_series_kernel(const uint32_t *__restrict__ samples, SeriesDesc *__restrict__ desc,
-                   const int32_t *__restrict__ order, uint32_t *__restrict__ keyA, uint32_t *__restrict__ keyB,
-                   uint16_t *__restrict__ labA, uint16_t *__restrict__ labB, int32_t *__restrict__ runs) {
-    __shared__ uint32_t s_wc[kSortWarps][256];  // per-warp digit counts, then offsets
-    __shared__ uint32_t s_base[256];            // running scatter base of each digit
-    __shared__ uint32_t s_hist[256];
-    __shared__ uint32_t s_tmp[32];
+// Warp-aggregated shared-memory histogram increment (callers pass the valid-lane mask).
+__device__ __forceinline__ void hist_add(uint32_t *h, uint32_t dg, unsigned vm) {
+    const unsigned peers = __match_any_sync(vm, dg);
+    if ((int)(__ffs(peers) - 1) == (int)(threadIdx.x & 31)) atomicAdd(h + dg, (uint32_t)__popc(peers));
+}
 
+struct SortSmem {
+    uint32_t wc[kSortWarps][256];  // per-warp digit counts -> tile-local offsets
+    uint32_t hist[256];            // digit counts of the current pass (whole series)
+    uint32_t hist2[256];           // digit counts of the next pass
+    uint32_t base[256];            // global start of each digit before the current tile
+    uint32_t tstart[256];          // tile-local start of each digit
+    uint32_t tcnt[256];            // tile digit counts
+    uint32_t key[kSortTile];       // tile staged in sorted order
+    uint16_t lab[kSortTile];
+    uint32_t tmp[32];
+};
+
+// LSD passes over one series.  COMP: keys are (value << 16) | step (value < 2^16), the
+// step label rides in the low half; otherwise keys are the values and labels travel in
+// their own arrays.  Pass p uses value bits [8p, 8p + 8).  Pass p reads (p == 0: the
+// input; odd p: B; even p: A) and writes the other buffer.  On entry sm.hist holds the
+// digit counts of pass 0.
+template <bool COMP>
+__device__ void lsd_passes(SortSmem &sm, int passes, const uint32_t *__restrict__ in, int32_t N, int32_t m,
+                           uint32_t *keyA, uint32_t *keyB, uint16_t *labA, uint16_t *labB) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int s = order[blockIdx.x];
-    const SeriesDesc d = desc[s];
-    const int64_t off = d.off;
-    const int32_t m = d.m;
-    const int32_t N = d.T * m;
-
-    // ---- largest value -> number of 8-bit passes (even, >= 2)
-    uint32_t vmax = 0;
-    for (int i = tid; i < N; i += kSortThreads) vmax = max(vmax, __ldg(samples + off + i));
-    vmax = __reduce_max_sync(kFull, vmax);
-    if (lane == 0) s_tmp[warp] = vmax;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t v = lane < kSortWarps ? s_tmp[lane] : 0u;
-        v = __reduce_max_sync(kFull, v);
-        if (lane == 0) s_tmp[31] = v;
-    }
-    __syncthreads();
-    vmax = s_tmp[31];
-    __syncthreads();
-    const int bits = vmax ? 32 - __clz(vmax) : 0;
-    int passes = (bits + 7) / 8;
-    passes = max(2, (passes + 1) & ~1);
-
     for (int p = 0; p < passes; p++) {
         const int shift = 8 * p;
-        const uint32_t *src_key = (p == 0) ? samples + off : ((p & 1) ? keyB : keyA) + off;
-        const uint16_t *src_lab = ((p & 1) ? labB : labA) + off;
-        uint32_t *dst_key = ((p & 1) ? keyA : keyB) + off;
-        uint16_t *dst_lab = ((p & 1) ? labA : labB) + off;
-
-        // digit histogram of the whole series
-        if (tid < 256) s_hist[tid] = 0;
+        const uint32_t *src_key = (p & 1) ? keyB : keyA;
+        const uint16_t *src_lab = (p & 1) ? labB : labA;
+        uint32_t *dst_key = (p & 1) ? keyA : keyB;
+        uint16_t *dst_lab = (p & 1) ? labA : labB;
+        const bool has_next = p + 1 < passes;
+        scan256(sm.hist, sm.base, sm.tmp);
+        if (tid < 256) sm.hist2[tid] = 0;
         __syncthreads();
-        for (int b0 = 0; b0 < N; b0 += kSortThreads) {
-            const int i = b0 + tid;
-            const bool valid = i < N;
-            const unsigned vm = __ballot_sync(kFull, valid);
-            if (valid) {
-                const uint32_t dg = (src_key[i] >> shift) & 255u;
-                const unsigned peers = __match_any_sync(vm, dg);
-                if ((int)(__ffs(peers) - 1) == lane) atomicAdd(&s_hist[dg], (uint32_t)__popc(peers));
-            }
-        }
-        __syncthreads();
-        scan256(s_hist, s_base, s_tmp);
-
         for (int tb = 0; tb < N; tb += kSortTile) {
-            for (int j = lane; j < 256; j += 32) s_wc[warp][j] = 0;
+            const int tn = min(kSortTile, N - tb);
+            for (int j = lane; j < 256; j += 32) sm.wc[warp][j] = 0;
             __syncwarp();
             uint32_t key[kSortItems], rk[kSortItems];
             uint16_t lb[kSortItems];
@@ -121,63 +104,154 @@ sort_series_kernel(const uint32_t *__restrict__ samples, SeriesDesc *__restrict_
                 lb[it] = 0;
                 rk[it] = 0;
                 if (valid) {
-                    key[it] = src_key[e];
-                    lb[it] = (p == 0) ? (uint16_t)(e / m) : src_lab[e];
+                    if (p == 0) {
+                        const uint32_t v = __ldg(in + e);
+                        const uint32_t t = (uint32_t)(e / m);
+                        key[it] = COMP ? ((v << 16) | t) : v;
+                        lb[it] = (uint16_t)t;
+                    } else {
+                        key[it] = src_key[e];
+                        if (!COMP) lb[it] = src_lab[e];
+                    }
                 }
                 const unsigned vm = __ballot_sync(kFull, valid);
                 if (valid) {
-                    const uint32_t dg = (key[it] >> shift) & 255u;
+                    const uint32_t val = COMP ? key[it] >> 16 : key[it];
+                    const uint32_t dg = (val >> shift) & 255u;
                     const unsigned peers = __match_any_sync(vm, dg);
                     const int leader = __ffs(peers) - 1;
                     uint32_t old = 0;
                     if (lane == leader) {
-                        old = s_wc[warp][dg];
-                        s_wc[warp][dg] = old + (uint32_t)__popc(peers);
+                        old = sm.wc[warp][dg];
+                        sm.wc[warp][dg] = old + (uint32_t)__popc(peers);
                     }
                     old = __shfl_sync(peers, old, leader);
                     rk[it] = old + (uint32_t)__popc(peers & lanemask_lt());
+                    if (has_next) hist_add(sm.hist2, (val >> (shift + 8)) & 255u, vm);
                 }
                 __syncwarp();
             }
             __syncthreads();
             if (tid < 256) {
-                uint32_t run = s_base[tid];
+                uint32_t tot = 0;
 #pragma unroll
-                for (int w = 0; w < kSortWarps; w++) {
-                    const uint32_t c = s_wc[w][tid];
-                    s_wc[w][tid] = run;
-                    run += c;
-                }
-                s_base[tid] = run;
+                for (int w = 0; w < kSortWarps; w++) tot += sm.wc[w][tid];
+                sm.tcnt[tid] = tot;
             }
             __syncthreads();
+            scan256(sm.tcnt, sm.tstart, sm.tmp);
+            if (tid < 256) {
+                uint32_t run = sm.tstart[tid];
+#pragma unroll
+                for (int w = 0; w < kSortWarps; w++) {
+                    const uint32_t c = sm.wc[w][tid];
+                    sm.wc[w][tid] = run;
+                    run += c;
+                }
+            }
+            __syncthreads();
+            // stage the tile in shared memory in sorted order
 #pragma unroll
             for (int it = 0; it < kSortItems; it++) {
                 const int e = tb + warp * (32 * kSortItems) + it * 32 + lane;
                 if (e < N) {
-                    const uint32_t dg = (key[it] >> shift) & 255u;
-                    const uint32_t pos = s_wc[warp][dg] + rk[it];
-                    dst_key[pos] = key[it];
-                    dst_lab[pos] = lb[it];
+                    const uint32_t val = COMP ? key[it] >> 16 : key[it];
+                    const uint32_t dg = (val >> shift) & 255u;
+                    const uint32_t local = sm.wc[warp][dg] + rk[it];
+                    sm.key[local] = key[it];
+                    if (!COMP) sm.lab[local] = lb[it];
                 }
             }
             __syncthreads();
+            // write out: consecutive tile positions of one digit go to consecutive addresses
+            for (int i = tid; i < tn; i += kSortThreads) {
+                const uint32_t k2 = sm.key[i];
+                const uint32_t dg = ((COMP ? k2 >> 16 : k2) >> shift) & 255u;
+                const uint32_t g = sm.base[dg] + (uint32_t)i - sm.tstart[dg];
+                dst_key[g] = k2;
+                if (!COMP) dst_lab[g] = sm.lab[i];
+            }
+            __syncthreads();
+            if (tid < 256) sm.base[tid] += sm.tcnt[tid];
+            __syncthreads();
+        }
+        if (tid < 256) sm.hist[tid] = sm.hist2[tid];
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kSortThreads, 2)
+sort_series_kernel(const uint32_t *__restrict__ samples, SeriesDesc *__restrict__ desc,
+                   const int32_t *__restrict__ order, uint32_t *__restrict__ keyA, uint32_t *__restrict__ keyB,
+                   uint16_t *__restrict__ labA, uint16_t *__restrict__ labB, int32_t *__restrict__ runs) {
+    __shared__ SortSmem sm;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int s = order[blockIdx.x];
+    const SeriesDesc d = desc[s];
+    const int64_t off = d.off;
+    const int32_t m = d.m;
+    const int32_t N = d.T * m;
+    const uint32_t *in = samples + off;
+
+    // ---- largest value and the digit counts of pass 0, in one read
+    if (tid < 256) sm.hist[tid] = 0;
+    __syncthreads();
+    uint32_t vmax = 0;
+    for (int b0 = 0; b0 < N; b0 += kSortThreads) {
+        const int i = b0 + tid;
+        const bool valid = i < N;
+        const unsigned vm = __ballot_sync(kFull, valid);
+        if (valid) {
+            const uint32_t v = __ldg(in + i);
+            vmax = max(vmax, v);
+            hist_add(sm.hist, v & 255u, vm);
         }
     }
+    vmax = __reduce_max_sync(kFull, vmax);
+    if (lane == 0) sm.tmp[warp] = vmax;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t v = lane < kSortWarps ? sm.tmp[lane] : 0u;
+        v = __reduce_max_sync(kFull, v);
+        if (lane == 0) sm.tmp[31] = v;
+    }
+    __syncthreads();
+    vmax = sm.tmp[31];
+    __syncthreads();
+    const int bits = vmax ? 32 - __clz(vmax) : 0;
+    const int passes = max(1, (bits + 7) / 8);
+    const bool comp = vmax < 65536u;
+    uint32_t *kA = keyA + off, *kB = keyB + off;
+    uint16_t *lA = labA + off, *lB = labB + off;
+    if (comp)
+        lsd_passes<true>(sm, passes, in, N, m, kA, kB, lA, lB);
+    else
+        lsd_passes<false>(sm, passes, in, N, m, kA, kB, lA, lB);
 
-    // ---- run table: start of every run of equal values, then N
-    const uint32_t *fk = keyA + off;
+    // ---- run table and final labels (into labA)
+    const uint32_t *fk = (passes & 1) ? kB : kA;
+    const uint16_t *flab = (passes & 1) ? lB : lA;
     int32_t *rt = runs + d.run_base;
     uint32_t count = 0;
     for (int tb = 0; tb < N; tb += kSortThreads) {
         const int i = tb + tid;
-        const bool flag = i < N && (i == 0 || fk[i] != fk[i - 1]);
+        bool flag = false;
+        if (i < N) {
+            const uint32_t k2 = fk[i];
+            const uint32_t v = comp ? k2 >> 16 : k2;
+            const uint32_t vp = i > 0 ? (comp ? fk[i - 1] >> 16 : fk[i - 1]) : ~v;
+            flag = (i == 0) || v != vp;
+            if (comp)
+                lA[i] = (uint16_t)(k2 & 0xffffu);
+            else if (passes & 1)
+                lA[i] = flab[i];
+        }
         const unsigned b = __ballot_sync(kFull, flag);
-        if (lane == 0) s_tmp[warp] = (uint32_t)__popc(b);
+        if (lane == 0) sm.tmp[warp] = (uint32_t)__popc(b);
         __syncthreads();
         uint32_t before = 0, total = 0;
         for (int w = 0; w < kSortWarps; w++) {
-            const uint32_t c = s_tmp[w];
+            const uint32_t c = sm.tmp[w];
             if (w < warp) before += c;
             total += c;
         }

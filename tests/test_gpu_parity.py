@@ -111,6 +111,26 @@ def test_medium_random_ragged_shapes(eng):
     check_segment(eng, b, 1e-2, 5, 8)
 
 
+def test_every_scan_tile(eng):
+    """Forced scan tiles (32, 64, 128 splits per warp item) give identical results."""
+    rng = np.random.default_rng(13)
+    series = []
+    for _ in range(40):
+        T = int(rng.integers(2, 700))
+        m = int(rng.integers(1, 7))
+        x = rng.integers(0, int(rng.integers(2, 300)), size=(T, m))
+        x[int(rng.integers(0, T)):] += int(rng.integers(0, 60))
+        series.append(x.astype(np.uint32))
+    b = synth.from_arrays(series)
+    try:
+        for kpt in (1, 2, 4):
+            eng.set_option(mt4g.OPT_SCAN_KPT, kpt)
+            check_scan(eng, b)
+            check_segment(eng, b, 1e-3, 2, 16)
+    finally:
+        eng.set_option(mt4g.OPT_SCAN_KPT, 0)
+
+
 def test_edge_values_and_shapes(eng):
     series = [
         np.zeros((2, 1), np.uint32),
