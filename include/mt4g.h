@@ -119,6 +119,73 @@ int mt4g_ks_segment(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offse
                     int32_t *cp_count, int32_t *cp_idx, int64_t *dnum, int64_t *dden, double *p,
                     void *cuda_stream);
 
+/* ------------------------------------------------------------------ learned proposal
+ *
+ * The paper scans every index (Sec. IV-B-1 (4)) and notes that candidate change points
+ * can be shortlisted first to save computation, a step MT4G omits because its datasets
+ * are small (Sec. IV-B-1, after step (4)).  The calls below build such a shortlist with a
+ * small 1D CNN over per-step summaries; the exact scan stays the judge of every answer.
+ *
+ * Features (mt4g_summaries): for each step t of a series, 17 values
+ *   i < 16: log2(q_i) - log2(med), q_i = the step's sorted sample at rank
+ *           min(m - 1, floor((i + 0.5) m / 16)), med = the series' sorted sample at N / 2;
+ *   16:     log2(1024 + 32 t) - 10 (the array size of the step);
+ * values below 1 read as 1; stored as BF16 bit patterns (round to nearest even) in rows
+ * of MT4G_FEAT_CHANNELS (channel 17 is zero).  Series s owns the rows
+ * [R_s, R_s + T_s + 4), R_s = sum_{s' < s} (T_s' + 4); step t is row R_s + 2 + t and the two
+ * rows on each side are zero.  m <= 256.
+ *
+ * Network: width-5 convolutions along the steps (zero padding 2), 18 -> 32 -> 32 -> 32 -> 1
+ * channels, ReLU after the first three, one logit per step (13,217 trained parameters).
+ * Weights are a flat FP32 vector of MT4G_CNN_PARAMS values: W1 [5][18][32], b1 [32],
+ * W2 [5][32][32], b2, W3 [5][32][32], b3, W4 [5][32][1], b4 [1] (tap-major, output
+ * channel fastest).  Kernels read BF16 roundings of the weights and of the activations
+ * and accumulate in FP32.
+ * Loss: softmax over a series' T steps, cross-entropy against the distribution uniform
+ * over its change points; series with none are left out; mean over the others.
+ * Training (mt4g_cnn_train_step): one batch of B series with a common T, Adam
+ * (lr, beta 0.9 / 0.999, eps 1e-8, bias correction) on the FP32 master weights.
+ */
+#define MT4G_FEAT_CHANNELS 18
+#define MT4G_CNN_PARAMS 13377
+
+/* Per-step features of every series (layout above) into feat_out (DEVICE, BF16 bits,
+ * [sum_s (T_s + 4)][18]).  Samples and host tables as for mt4g_ks_scan. */
+int mt4g_summaries(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets, const int32_t *steps,
+                   int64_t S, uint16_t *feat_out, void *cuda_stream);
+
+/* Initialise the weights (He-uniform from splitmix64(seed), zero biases) and the Adam state. */
+int mt4g_cnn_init(mt4g_ctx *ctx, uint64_t seed);
+/* Copy the FP32 master weights to / from a HOST array of MT4G_CNN_PARAMS floats. */
+int mt4g_cnn_get_params(mt4g_ctx *ctx, float *host_out);
+int mt4g_cnn_set_params(mt4g_ctx *ctx, const float *host_in);
+/* Weights file: header (magic, sizes, Adam step, CRC-32) + weights + Adam moments.
+ * Loading checks the header and the checksum (MT4G_EINVAL on mismatch). */
+int mt4g_cnn_save(mt4g_ctx *ctx, const char *path);
+int mt4g_cnn_load(mt4g_ctx *ctx, const char *path);
+
+/* Logits of every step: feat (DEVICE, layout above), steps (HOST int32 [S]);
+ * logits_out (DEVICE float, one per feature row; pad rows are not written). */
+int mt4g_cnn_forward(mt4g_ctx *ctx, const uint16_t *feat, const int32_t *steps, int64_t S, float *logits_out,
+                     void *cuda_stream);
+
+/* Loss and gradients of a batch of B series with T steps each (feat: B (T + 4) rows).
+ * cp_count (DEVICE int32 [B]) and cp_idx (DEVICE int32 [B * max_cp]) give each series'
+ * change points.  grad_out: DEVICE float [MT4G_CNN_PARAMS]; loss_out: DEVICE float or NULL. */
+int mt4g_cnn_grads(mt4g_ctx *ctx, const uint16_t *feat, int32_t T, int64_t B, const int32_t *cp_count,
+                   const int32_t *cp_idx, int32_t max_cp, float *grad_out, float *loss_out, void *cuda_stream);
+/* The same forward and backward pass followed by one Adam update. */
+int mt4g_cnn_train_step(mt4g_ctx *ctx, const uint16_t *feat, int32_t T, int64_t B, const int32_t *cp_count,
+                        const int32_t *cp_idx, int32_t max_cp, float lr, float *loss_out, void *cuda_stream);
+
+/* Change-point windows of every series: features, logits, softmax over the steps, then
+ * n_win (<= 8) times the largest remaining logit (smallest step on ties) as a centre c,
+ * removing the steps within +-half_width of it.  win_center: DEVICE int32 [S * n_win]
+ * (-1 when fewer windows exist); conf: DEVICE float [S], the softmax mass of the union of
+ * the windows [c - half_width, c + half_width]. */
+int mt4g_propose(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets, const int32_t *steps, int64_t S,
+                 int32_t n_win, int32_t half_width, int32_t *win_center, float *conf, void *cuda_stream);
+
 /*
  * Measurement helpers (no counterpart in the paper; they instrument the calls above).
  *

@@ -22,6 +22,8 @@ OPT_WAIT_LIMIT_NS = 1
 OPT_STAGE_TIMING = 2
 OPT_SCAN_KPT = 3
 MAX_STEPS = 32768
+FEAT_CHANNELS = 18
+CNN_PARAMS = 13377
 
 _lib = None
 
@@ -58,6 +60,16 @@ def load_library():
     L.mt4g_ks_segment.argtypes = [vp, vp, vp, vp, i64, dbl, i32, i32, i32, vp, vp, vp, vp, vp, vp]
     L.mt4g_stage_times.argtypes = [vp, vp, i32]
     L.mt4g_last_work.argtypes = [vp, vp]
+    L.mt4g_summaries.argtypes = [vp, vp, vp, vp, i64, vp, vp]
+    L.mt4g_cnn_init.argtypes = [vp, ctypes.c_uint64]
+    L.mt4g_cnn_get_params.argtypes = [vp, vp]
+    L.mt4g_cnn_set_params.argtypes = [vp, vp]
+    L.mt4g_cnn_save.argtypes = [vp, ctypes.c_char_p]
+    L.mt4g_cnn_load.argtypes = [vp, ctypes.c_char_p]
+    L.mt4g_cnn_forward.argtypes = [vp, vp, vp, i64, vp, vp]
+    L.mt4g_cnn_grads.argtypes = [vp, vp, i32, i64, vp, vp, i32, vp, vp, vp]
+    L.mt4g_cnn_train_step.argtypes = [vp, vp, i32, i64, vp, vp, i32, ctypes.c_float, vp, vp]
+    L.mt4g_propose.argtypes = [vp, vp, vp, vp, i64, i32, i32, vp, vp, vp]
     _lib = L
     return L
 
@@ -65,7 +77,9 @@ def load_library():
 def exported_symbols():
     """Names the header declares; the tests check the library exports each of them."""
     return ["mt4g_create", "mt4g_destroy", "mt4g_last_error", "mt4g_wait", "mt4g_set_option",
-            "mt4g_ks_scan", "mt4g_ks_segment", "mt4g_stage_times", "mt4g_last_work"]
+            "mt4g_ks_scan", "mt4g_ks_segment", "mt4g_stage_times", "mt4g_last_work",
+            "mt4g_summaries", "mt4g_cnn_init", "mt4g_cnn_get_params", "mt4g_cnn_set_params", "mt4g_cnn_save",
+            "mt4g_cnn_load", "mt4g_cnn_forward", "mt4g_cnn_grads", "mt4g_cnn_train_step", "mt4g_propose"]
 
 
 class ScanResult(NamedTuple):
@@ -204,6 +218,97 @@ class Engine:
             if status not in (OK, ECAPACITY):
                 self._check(status)
         return out._replace(rc=status)
+
+
+def feature_rows(steps) -> int:
+    """Rows of the padded feature layout: sum over series of T_s + 4."""
+    steps = np.asarray(steps, np.int64)
+    return int(steps.sum() + 4 * steps.shape[0])
+
+
+def _mixin_learned(cls):
+    """Learned-proposal calls of Engine (kept apart for readability)."""
+
+    def summaries(self, samples, offsets, steps, stream=None, out=None, sync=True):
+        import torch
+        offsets, steps = _host_tables(offsets, steps)
+        rows = feature_rows(steps)
+        if out is None:
+            out = torch.empty((rows, FEAT_CHANNELS), dtype=torch.int16, device=samples.device)
+        self._check(self._L.mt4g_summaries(self._h, _dev_ptr(samples, "samples"),
+                                           offsets.ctypes.data_as(ctypes.c_void_p),
+                                           steps.ctypes.data_as(ctypes.c_void_p), steps.shape[0],
+                                           _dev_ptr(out, "feat"), _stream_handle(stream)))
+        if sync:
+            self._check(self.wait())
+        return out
+
+    def cnn_init(self, seed: int):
+        self._check(self._L.mt4g_cnn_init(self._h, int(seed)))
+
+    def cnn_get_params(self) -> np.ndarray:
+        w = np.zeros(CNN_PARAMS, np.float32)
+        self._check(self._L.mt4g_cnn_get_params(self._h, w.ctypes.data_as(ctypes.c_void_p)))
+        return w
+
+    def cnn_set_params(self, w: np.ndarray):
+        w = np.ascontiguousarray(w, np.float32)
+        assert w.shape == (CNN_PARAMS,)
+        self._check(self._L.mt4g_cnn_set_params(self._h, w.ctypes.data_as(ctypes.c_void_p)))
+
+    def cnn_save(self, path: str):
+        self._check(self._L.mt4g_cnn_save(self._h, os.fsencode(path)))
+
+    def cnn_load(self, path: str):
+        self._check(self._L.mt4g_cnn_load(self._h, os.fsencode(path)))
+
+    def cnn_forward(self, feat, steps, stream=None, out=None):
+        import torch
+        steps = np.ascontiguousarray(steps, np.int32)
+        if out is None:
+            out = torch.zeros(feature_rows(steps), dtype=torch.float32, device=feat.device)
+        self._check(self._L.mt4g_cnn_forward(self._h, _dev_ptr(feat, "feat"), steps.ctypes.data_as(ctypes.c_void_p),
+                                             steps.shape[0], _dev_ptr(out, "logits"), _stream_handle(stream)))
+        return out
+
+    def cnn_grads(self, feat, T, B, cp_count, cp_idx, stream=None):
+        import torch
+        grad = torch.zeros(CNN_PARAMS, dtype=torch.float32, device=feat.device)
+        loss = torch.zeros(1, dtype=torch.float32, device=feat.device)
+        self._check(self._L.mt4g_cnn_grads(self._h, _dev_ptr(feat, "feat"), int(T), int(B),
+                                           _dev_ptr(cp_count, "cp_count"), _dev_ptr(cp_idx, "cp_idx"),
+                                           int(cp_idx.shape[-1]), _dev_ptr(grad, "grad"), _dev_ptr(loss, "loss"),
+                                           _stream_handle(stream)))
+        return grad, loss
+
+    def cnn_train_step(self, feat, T, B, cp_count, cp_idx, lr=1e-3, loss=None, stream=None):
+        self._check(self._L.mt4g_cnn_train_step(self._h, _dev_ptr(feat, "feat"), int(T), int(B),
+                                                _dev_ptr(cp_count, "cp_count"), _dev_ptr(cp_idx, "cp_idx"),
+                                                int(cp_idx.shape[-1]), ctypes.c_float(lr),
+                                                _dev_ptr(loss, "loss") if loss is not None else None,
+                                                _stream_handle(stream)))
+
+    def propose(self, samples, offsets, steps, n_win=3, half_width=16, stream=None, sync=True):
+        import torch
+        offsets, steps = _host_tables(offsets, steps)
+        S = steps.shape[0]
+        win = torch.empty((S, n_win), dtype=torch.int32, device=samples.device)
+        conf = torch.empty(S, dtype=torch.float32, device=samples.device)
+        self._check(self._L.mt4g_propose(self._h, _dev_ptr(samples, "samples"),
+                                         offsets.ctypes.data_as(ctypes.c_void_p),
+                                         steps.ctypes.data_as(ctypes.c_void_p), S, int(n_win), int(half_width),
+                                         _dev_ptr(win, "win"), _dev_ptr(conf, "conf"), _stream_handle(stream)))
+        if sync:
+            self._check(self.wait())
+        return win, conf
+
+    for name, fn in list(locals().items()):
+        if callable(fn) and not name.startswith("_"):
+            setattr(cls, name, fn)
+    return cls
+
+
+Engine = _mixin_learned(Engine)
 
 
 def to_device_samples(samples: np.ndarray, device="cuda"):

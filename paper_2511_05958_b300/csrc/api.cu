@@ -10,7 +10,7 @@
 #include <string>
 #include <vector>
 
-#include "mt4g_internal.cuh"
+#include "mt4g_cnn.cuh"
 
 using namespace mt4g;
 
@@ -31,6 +31,13 @@ struct mt4g_ctx {
     bool last_enqueued = false;  // the most recent call enqueued work (its status is in h_hdr)
 
     int32_t forced_kpt = 0;  // 0: per-series choice; 1, 2, 4: every series
+
+    // proposal network
+    CnnState cnn;
+    bool cnn_alloc = false;
+    bool cnn_ready = false;  // weights initialised or loaded
+    void *cnn_ws = nullptr;  // activations, features, host-table copies
+    size_t cnn_ws_bytes = 0;
 
     // stage timing: events of the last kTimingRing calls
     static constexpr int kTimingRing = 64;
@@ -418,6 +425,8 @@ void mt4g_destroy(mt4g_ctx *c) {
         cudaEventDestroy(c->pin_free);
     }
     if (c->ws) cudaFree(c->ws);
+    if (c->cnn_ws) cudaFree(c->cnn_ws);
+    if (c->cnn_alloc) cudaFree(c->cnn.master);
     if (c->pin) cudaFreeHost(c->pin);
     if (c->h_hdr) cudaFreeHost(c->h_hdr);
     if (c->events_made)
@@ -546,6 +555,396 @@ int mt4g_last_work(mt4g_ctx *c, int64_t *evals) {
     if (!c || !evals) return MT4G_EINVAL;
     *evals = (int64_t)c->h_hdr->evals;
     return MT4G_OK;
+}
+
+}  // extern "C"
+
+// ====================================================================== proposal network
+
+namespace {
+
+int ensure_cnn_state(mt4g_ctx *c) {
+    if (c->cnn_alloc) return MT4G_OK;
+    float *base = nullptr;
+    const size_t n = (size_t)kCnnParams;
+    // master, used, flipped (2 x 5120), m1, m2, grad, loss, then FP64 gradients
+    const size_t nf = 6 * n + 2 * 5120 + 64;
+    CUDA_TRY(c, cudaMalloc(&base, nf * sizeof(float) + n * sizeof(double) + 256));
+    CnnState &W = c->cnn;
+    W.master = base;
+    W.used = base + n;
+    W.m1 = base + 2 * n;
+    W.m2 = base + 3 * n;
+    W.grad = base + 4 * n;
+    W.flipped = base + 5 * n;
+    W.loss = base + 5 * n + 2 * 5120;
+    W.grad64 = (double *)(((uintptr_t)(base + nf) + 255) & ~(uintptr_t)255);
+    CUDA_TRY(c, cudaMemset(base, 0, nf * sizeof(float)));
+    c->cnn_alloc = true;
+    return MT4G_OK;
+}
+
+struct CnnBuffers {
+    CnnActs A;
+    uint16_t *feat;
+    SeriesDesc *desc;
+    int64_t *tiles_before;
+    int32_t *win;
+    float *conf;
+};
+
+// Layout of the proposal workspace for `rows` padded rows and S series.
+size_t carve_cnn(void *base, int64_t rows, int64_t S, bool training, bool own_feat, int32_t n_win, CnnBuffers &B) {
+    Carver c(base);
+    B.A.a1 = c.take<uint16_t>(rows * 32);
+    B.A.a2 = c.take<uint16_t>(rows * 32);
+    B.A.a3 = c.take<uint16_t>(rows * 32);
+    B.A.logits = c.take<float>(rows);
+    B.A.g = c.take<float>(training ? rows : 0);
+    B.A.dz1 = c.take<float>(training ? rows * 32 : 0);
+    B.A.dz2 = c.take<float>(training ? rows * 32 : 0);
+    B.A.dz3 = c.take<float>(training ? rows * 32 : 0);
+    B.A.inv_valid = c.take<float>(16);
+    B.tiles_before = c.take<int64_t>(S);
+    B.A.tiles_before = B.tiles_before;
+    B.desc = c.take<SeriesDesc>(S);
+    B.feat = c.take<uint16_t>(own_feat ? rows * kFeatC : 0);
+    B.win = c.take<int32_t>(own_feat ? S * n_win : 0);
+    B.conf = c.take<float>(own_feat ? S : 0);
+    return c.off + 256;
+}
+
+int ensure_cnn_ws(mt4g_ctx *c, size_t bytes) {
+    if (bytes <= c->cnn_ws_bytes) return MT4G_OK;
+    if (c->have_last) CUDA_TRY(c, cudaStreamSynchronize(c->last_stream));
+    if (c->cnn_ws) cudaFree(c->cnn_ws);
+    c->cnn_ws = nullptr;
+    c->cnn_ws_bytes = 0;
+    const size_t want = bytes + bytes / 8;
+    CUDA_TRY(c, cudaMalloc(&c->cnn_ws, want));
+    c->cnn_ws_bytes = want;
+    return MT4G_OK;
+}
+
+// Host tables of a feature batch: descriptors (step bases) and tile prefixes.
+int upload_cnn_tables(mt4g_ctx *c, const std::vector<SeriesDesc> &desc, CnnBuffers &B, int64_t *ntiles,
+                      cudaStream_t st) {
+    std::vector<int64_t> tb;
+    *ntiles = cnn_tiles(desc, tb);
+    const size_t S = desc.size();
+    int rc = ensure_pinned(c, S * (sizeof(SeriesDesc) + sizeof(int64_t)) + 64);
+    if (rc) return rc;
+    char *h = (char *)c->pin;
+    memcpy(h, desc.data(), S * sizeof(SeriesDesc));
+    memcpy(h + S * sizeof(SeriesDesc), tb.data(), S * sizeof(int64_t));
+    CUDA_TRY(c, cudaMemcpyAsync(B.desc, h, S * sizeof(SeriesDesc), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(c, cudaMemcpyAsync(B.tiles_before, h + S * sizeof(SeriesDesc), S * sizeof(int64_t),
+                                cudaMemcpyHostToDevice, st));
+    CUDA_TRY(c, cudaEventRecord(c->pin_free, st));
+    return MT4G_OK;
+}
+
+int zero_pads(mt4g_ctx *c, CnnBuffers &B, int64_t S, bool training, cudaStream_t st) {
+    CUDA_TRY(c, launch_zero_pad_rows(B.A.a1, 64, B.desc, S, st));
+    CUDA_TRY(c, launch_zero_pad_rows(B.A.a2, 64, B.desc, S, st));
+    CUDA_TRY(c, launch_zero_pad_rows(B.A.a3, 64, B.desc, S, st));
+    if (training) {
+        CUDA_TRY(c, launch_zero_pad_rows(B.A.g, 4, B.desc, S, st));
+        CUDA_TRY(c, launch_zero_pad_rows(B.A.dz1, 128, B.desc, S, st));
+        CUDA_TRY(c, launch_zero_pad_rows(B.A.dz2, 128, B.desc, S, st));
+        CUDA_TRY(c, launch_zero_pad_rows(B.A.dz3, 128, B.desc, S, st));
+    }
+    return MT4G_OK;
+}
+
+std::vector<SeriesDesc> feature_desc(const int32_t *steps, int64_t S) {
+    std::vector<SeriesDesc> d(S);
+    int64_t sb = 0;
+    for (int64_t s = 0; s < S; s++) {
+        d[s] = SeriesDesc{};
+        d[s].T = steps[s];
+        d[s].m = 1;
+        d[s].step_base = sb;
+        sb += steps[s];
+    }
+    return d;
+}
+
+int check_steps(mt4g_ctx *c, const int32_t *steps, int64_t S) {
+    if (S < 0 || (S > 0 && !steps)) return fail(c, MT4G_EINVAL, "bad steps table");
+    for (int64_t s = 0; s < S; s++)
+        if (steps[s] < 2 || steps[s] > MT4G_MAX_STEPS) return fail(c, MT4G_EINVAL, "series %lld: bad T", (long long)s);
+    return MT4G_OK;
+}
+
+// He-uniform initial weights from splitmix64(seed, index); zero biases.
+void init_weights_host(uint64_t seed, std::vector<float> &w) {
+    w.assign(kCnnParams, 0.f);
+    const int cins[4] = {17, 32, 32, 32}, cinp[4] = {kFeatC, 32, 32, 32}, couts[4] = {32, 32, 32, 1};
+    uint64_t x = seed * 0x9E3779B97F4A7C15ULL + 0x632BE59BD9B4E019ULL;
+    for (int l = 0; l < 4; l++) {
+        const float bound = sqrtf(6.f / (float)(cins[l] * 5));
+        const int off = cnn_off(2 * l);
+        for (int dd = 0; dd < 5; dd++)
+            for (int i = 0; i < cinp[l]; i++)
+                for (int o = 0; o < couts[l]; o++) {
+                    uint64_t z = (x += 0x9E3779B97F4A7C15ULL);
+                    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+                    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+                    z ^= z >> 31;
+                    const float u = (float)((z >> 40) * 0x1.0p-24);  // [0, 1)
+                    w[off + (dd * cinp[l] + i) * couts[l] + o] = i < cins[l] ? (2.f * u - 1.f) * bound : 0.f;
+                }
+    }
+}
+
+uint32_t crc32_update(uint32_t crc, const void *data, size_t n) {
+    const uint8_t *p = (const uint8_t *)data;
+    crc = ~crc;
+    for (size_t i = 0; i < n; i++) {
+        crc ^= p[i];
+        for (int k = 0; k < 8; k++) crc = (crc >> 1) ^ (0xEDB88320u & (0u - (crc & 1u)));
+    }
+    return ~crc;
+}
+
+struct CnnFileHeader {
+    char magic[8];  // "MT4GCNN1"
+    int32_t n_params;
+    int32_t feat_channels;
+    int64_t adam_step;
+    uint32_t crc;  // CRC-32 of the three arrays that follow
+    uint32_t pad;
+};
+
+}  // namespace
+
+extern "C" {
+
+int mt4g_cnn_init(mt4g_ctx *c, uint64_t seed) {
+    int rc = begin_call(c);
+    if (rc) return rc;
+    rc = ensure_cnn_state(c);
+    if (rc) return rc;
+    std::vector<float> w;
+    init_weights_host(seed, w);
+    CUDA_TRY(c, cudaMemcpy(c->cnn.master, w.data(), kCnnParams * sizeof(float), cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemset(c->cnn.m1, 0, kCnnParams * sizeof(float)));
+    CUDA_TRY(c, cudaMemset(c->cnn.m2, 0, kCnnParams * sizeof(float)));
+    c->cnn.step = 0;
+    c->cnn_ready = true;
+    return MT4G_OK;
+}
+
+int mt4g_cnn_get_params(mt4g_ctx *c, float *host_out) {
+    int rc = begin_call(c);
+    if (rc) return rc;
+    if (!c->cnn_ready) return fail(c, MT4G_EINVAL, "no weights: call mt4g_cnn_init or mt4g_cnn_load");
+    if (!host_out) return fail(c, MT4G_EINVAL, "NULL output");
+    if (c->have_last) CUDA_TRY(c, cudaStreamSynchronize(c->last_stream));
+    CUDA_TRY(c, cudaMemcpy(host_out, c->cnn.master, kCnnParams * sizeof(float), cudaMemcpyDeviceToHost));
+    return MT4G_OK;
+}
+
+int mt4g_cnn_set_params(mt4g_ctx *c, const float *host_in) {
+    int rc = begin_call(c);
+    if (rc) return rc;
+    if (!host_in) return fail(c, MT4G_EINVAL, "NULL input");
+    rc = ensure_cnn_state(c);
+    if (rc) return rc;
+    if (c->have_last) CUDA_TRY(c, cudaStreamSynchronize(c->last_stream));
+    CUDA_TRY(c, cudaMemcpy(c->cnn.master, host_in, kCnnParams * sizeof(float), cudaMemcpyHostToDevice));
+    c->cnn_ready = true;
+    return MT4G_OK;
+}
+
+int mt4g_cnn_save(mt4g_ctx *c, const char *path) {
+    int rc = begin_call(c);
+    if (rc) return rc;
+    if (!c->cnn_ready) return fail(c, MT4G_EINVAL, "no weights to save");
+    if (!path) return fail(c, MT4G_EINVAL, "NULL path");
+    if (c->have_last) CUDA_TRY(c, cudaStreamSynchronize(c->last_stream));
+    std::vector<float> buf(3 * (size_t)kCnnParams);
+    CUDA_TRY(c, cudaMemcpy(buf.data(), c->cnn.master, kCnnParams * sizeof(float), cudaMemcpyDeviceToHost));
+    CUDA_TRY(c, cudaMemcpy(buf.data() + kCnnParams, c->cnn.m1, kCnnParams * sizeof(float), cudaMemcpyDeviceToHost));
+    CUDA_TRY(c, cudaMemcpy(buf.data() + 2 * kCnnParams, c->cnn.m2, kCnnParams * sizeof(float),
+                           cudaMemcpyDeviceToHost));
+    CnnFileHeader h{};
+    memcpy(h.magic, "MT4GCNN1", 8);
+    h.n_params = kCnnParams;
+    h.feat_channels = kFeatC;
+    h.adam_step = c->cnn.step;
+    h.crc = crc32_update(0, buf.data(), buf.size() * sizeof(float));
+    FILE *f = fopen(path, "wb");
+    if (!f) return fail(c, MT4G_EINVAL, "cannot open %s for writing", path);
+    const bool ok = fwrite(&h, sizeof(h), 1, f) == 1 && fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    fclose(f);
+    return ok ? MT4G_OK : fail(c, MT4G_EINVAL, "short write to %s", path);
+}
+
+int mt4g_cnn_load(mt4g_ctx *c, const char *path) {
+    int rc = begin_call(c);
+    if (rc) return rc;
+    if (!path) return fail(c, MT4G_EINVAL, "NULL path");
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(c, MT4G_EINVAL, "cannot open %s", path);
+    CnnFileHeader h{};
+    std::vector<float> buf(3 * (size_t)kCnnParams);
+    const bool ok = fread(&h, sizeof(h), 1, f) == 1 && fread(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    fclose(f);
+    if (!ok || memcmp(h.magic, "MT4GCNN1", 8) != 0 || h.n_params != kCnnParams || h.feat_channels != kFeatC)
+        return fail(c, MT4G_EINVAL, "%s is not a weights file of this network", path);
+    if (crc32_update(0, buf.data(), buf.size() * sizeof(float)) != h.crc)
+        return fail(c, MT4G_EINVAL, "%s: checksum mismatch", path);
+    rc = ensure_cnn_state(c);
+    if (rc) return rc;
+    if (c->have_last) CUDA_TRY(c, cudaStreamSynchronize(c->last_stream));
+    CUDA_TRY(c, cudaMemcpy(c->cnn.master, buf.data(), kCnnParams * sizeof(float), cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemcpy(c->cnn.m1, buf.data() + kCnnParams, kCnnParams * sizeof(float), cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemcpy(c->cnn.m2, buf.data() + 2 * kCnnParams, kCnnParams * sizeof(float),
+                           cudaMemcpyHostToDevice));
+    c->cnn.step = h.adam_step;
+    c->cnn_ready = true;
+    return MT4G_OK;
+}
+
+int mt4g_summaries(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets, const int32_t *steps, int64_t S,
+                   uint16_t *feat_out, void *cuda_stream) {
+    int rc = begin_call(ctx);
+    if (rc) return rc;
+    if (S > 0 && (!samples || !feat_out)) return fail(ctx, MT4G_EINVAL, "NULL device pointer");
+    Plan P;
+    rc = make_plan(ctx, offsets, steps, S, MT4G_MODE_FULL, 1, P);
+    if (rc) return rc;
+    for (int64_t s = 0; s < S; s++)
+        if (P.desc[s].m > 256) return fail(ctx, MT4G_EINVAL, "series %lld: summaries need m <= 256", (long long)s);
+    if (S == 0) return MT4G_OK;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    Buffers B;
+    RunParams R;
+    mark(ctx, 0, st);
+    const int epoch = enqueue_pipeline(ctx, samples, P, R, B, st);
+    if (epoch < 0) return epoch;
+    CUDA_TRY(ctx, launch_summaries(samples, B.desc, S, feat_out, st));
+    mark(ctx, 3, st);
+    return finish_call(ctx, B, st);
+}
+
+int mt4g_cnn_forward(mt4g_ctx *c, const uint16_t *feat, const int32_t *steps, int64_t S, float *logits_out,
+                     void *cuda_stream) {
+    int rc = begin_call(c);
+    if (rc) return rc;
+    if (!c->cnn_ready) return fail(c, MT4G_EINVAL, "no weights: call mt4g_cnn_init or mt4g_cnn_load");
+    rc = check_steps(c, steps, S);
+    if (rc) return rc;
+    if (S == 0) return MT4G_OK;
+    if (!feat || !logits_out) return fail(c, MT4G_EINVAL, "NULL device pointer");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    std::vector<SeriesDesc> desc = feature_desc(steps, S);
+    const int64_t rows = desc.back().step_base + desc.back().T + 4 * S;
+    CnnBuffers B;
+    const size_t need = carve_cnn(nullptr, rows, S, false, false, 0, B);
+    rc = ensure_cnn_ws(c, need);
+    if (rc) return rc;
+    carve_cnn(c->cnn_ws, rows, S, false, false, 0, B);
+    B.A.logits = logits_out;
+    int64_t ntiles = 0;
+    rc = upload_cnn_tables(c, desc, B, &ntiles, st);
+    if (rc) return rc;
+    rc = zero_pads(c, B, S, false, st);
+    if (rc) return rc;
+    CUDA_TRY(c, cnn_prepare(c->cnn, st));
+    CUDA_TRY(c, cnn_forward(c->cnn, feat, B.A, B.desc, B.tiles_before, S, ntiles, st));
+    c->last_stream = st;
+    c->have_last = true;
+    return MT4G_OK;
+}
+
+// Forward + backward on a batch of B series with T steps each (features in the padded
+// layout); gradients into grad_out (device, kCnnParams) or the context's scratch.
+static int cnn_fwd_bwd(mt4g_ctx *c, const uint16_t *feat, int32_t T, int64_t Bn, const int32_t *cp_count,
+                       const int32_t *cp_idx, int32_t max_cp, float *grad_out, float *loss_out, cudaStream_t st) {
+    if (!c->cnn_ready) return fail(c, MT4G_EINVAL, "no weights: call mt4g_cnn_init or mt4g_cnn_load");
+    if (T < 2 || T > MT4G_MAX_STEPS || Bn < 1 || max_cp < 1 || !feat || !cp_count || !cp_idx)
+        return fail(c, MT4G_EINVAL, "bad training batch arguments");
+    std::vector<int32_t> steps(Bn, T);
+    std::vector<SeriesDesc> desc = feature_desc(steps.data(), Bn);
+    const int64_t rows = Bn * (int64_t)(T + 4);
+    CnnBuffers B;
+    const size_t need = carve_cnn(nullptr, rows, Bn, true, false, 0, B);
+    int rc = ensure_cnn_ws(c, need);
+    if (rc) return rc;
+    carve_cnn(c->cnn_ws, rows, Bn, true, false, 0, B);
+    int64_t ntiles = 0;
+    rc = upload_cnn_tables(c, desc, B, &ntiles, st);
+    if (rc) return rc;
+    rc = zero_pads(c, B, Bn, true, st);
+    if (rc) return rc;
+    CUDA_TRY(c, cnn_prepare(c->cnn, st));
+    CUDA_TRY(c, cnn_forward(c->cnn, feat, B.A, B.desc, B.tiles_before, Bn, ntiles, st));
+    CUDA_TRY(c, cnn_backward(c->cnn, feat, B.A, cp_count, cp_idx, max_cp, B.desc, Bn, T, grad_out,
+                             loss_out ? loss_out : c->cnn.loss, st));
+    c->last_stream = st;
+    c->have_last = true;
+    return MT4G_OK;
+}
+
+int mt4g_cnn_grads(mt4g_ctx *c, const uint16_t *feat, int32_t T, int64_t B, const int32_t *cp_count,
+                   const int32_t *cp_idx, int32_t max_cp, float *grad_out, float *loss_out, void *cuda_stream) {
+    int rc = begin_call(c);
+    if (rc) return rc;
+    if (!grad_out) return fail(c, MT4G_EINVAL, "NULL gradient buffer");
+    return cnn_fwd_bwd(c, feat, T, B, cp_count, cp_idx, max_cp, grad_out, loss_out, (cudaStream_t)cuda_stream);
+}
+
+int mt4g_cnn_train_step(mt4g_ctx *c, const uint16_t *feat, int32_t T, int64_t B, const int32_t *cp_count,
+                        const int32_t *cp_idx, int32_t max_cp, float lr, float *loss_out, void *cuda_stream) {
+    int rc = begin_call(c);
+    if (rc) return rc;
+    if (!(lr > 0.f)) return fail(c, MT4G_EINVAL, "learning rate must be > 0");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    rc = cnn_fwd_bwd(c, feat, T, B, cp_count, cp_idx, max_cp, c->cnn.grad, loss_out, st);
+    if (rc) return rc;
+    CUDA_TRY(c, cnn_adam(c->cnn, c->cnn.grad, lr, st));
+    return MT4G_OK;
+}
+
+int mt4g_propose(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets, const int32_t *steps, int64_t S,
+                 int32_t n_win, int32_t half_width, int32_t *win_center, float *conf, void *cuda_stream) {
+    int rc = begin_call(ctx);
+    if (rc) return rc;
+    if (!ctx->cnn_ready) return fail(ctx, MT4G_EINVAL, "no weights: call mt4g_cnn_init or mt4g_cnn_load");
+    if (n_win < 1 || n_win > 8 || half_width < 0) return fail(ctx, MT4G_EINVAL, "need 1 <= n_win <= 8, half >= 0");
+    if (S > 0 && (!samples || !win_center || !conf)) return fail(ctx, MT4G_EINVAL, "NULL device pointer");
+    Plan P;
+    rc = make_plan(ctx, offsets, steps, S, MT4G_MODE_FULL, 1, P);
+    if (rc) return rc;
+    for (int64_t s = 0; s < S; s++)
+        if (P.desc[s].m > 256) return fail(ctx, MT4G_EINVAL, "series %lld: proposals need m <= 256", (long long)s);
+    if (S == 0) return MT4G_OK;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    Buffers B;
+    RunParams R;
+    mark(ctx, 0, st);
+    const int epoch = enqueue_pipeline(ctx, samples, P, R, B, st);
+    if (epoch < 0) return epoch;
+    const int64_t rows = P.sumT + 4 * S;
+    CnnBuffers C;
+    const size_t need = carve_cnn(nullptr, rows, S, false, true, n_win, C);
+    rc = ensure_cnn_ws(ctx, need);
+    if (rc) return rc;
+    carve_cnn(ctx->cnn_ws, rows, S, false, true, n_win, C);
+    int64_t ntiles = 0;
+    rc = upload_cnn_tables(ctx, P.desc, C, &ntiles, st);
+    if (rc) return rc;
+    rc = zero_pads(ctx, C, S, false, st);
+    if (rc) return rc;
+    CUDA_TRY(ctx, launch_summaries(samples, B.desc, S, C.feat, st));
+    CUDA_TRY(ctx, cnn_prepare(ctx->cnn, st));
+    CUDA_TRY(ctx, cnn_forward(ctx->cnn, C.feat, C.A, B.desc, C.tiles_before, S, ntiles, st));
+    CUDA_TRY(ctx, launch_propose(C.A.logits, B.desc, S, n_win, half_width, win_center, conf, st));
+    mark(ctx, 3, st);
+    return finish_call(ctx, B, st);
 }
 
 }  // extern "C"

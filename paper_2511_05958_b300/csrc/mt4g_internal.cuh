@@ -32,7 +32,15 @@ struct SeriesDesc {
     int32_t m;          // samples per step
     int32_t nruns;      // U_s, number of distinct values (written by the sort)
     int32_t kpt;        // split groups of 32 per warp work item (1, 2 or 4): the scan tile
+    uint32_t median;    // sorted value at index N / 2 (written by the sort)
+    int32_t pad;
 };
+
+// Learned-proposal feature rows: series s owns rows [row_base(s), row_base(s) + T_s + 4) of
+// an [rows][kFeatC] array; step t is row row_base(s) + 2 + t and the two rows on each
+// side are zero, so width-5 convolutions need no bounds checks.
+constexpr int kFeatC = 18;  // 16 quantiles + step size + one zero channel
+__host__ __device__ inline int64_t row_base(const SeriesDesc &d, int64_t s) { return d.step_base + 4 * s; }
 
 // One unit of work: the splits of slice `chunk` of segment [lo, hi) of a series.
 // With w = 32 kpt splits per slice, slice c covers k in [lo + min_seg + w c, ... + w - 1],
@@ -109,6 +117,9 @@ cudaError_t launch_collect(const SeriesDesc *desc, int64_t S, const uint8_t *cp_
                            const int64_t *cp_den, const double *cp_p, int32_t max_cp, int32_t *cp_count,
                            int32_t *cp_idx, int64_t *dnum, int64_t *dden, double *p, QueueHeader *q,
                            cudaStream_t st);
+
+cudaError_t launch_summaries(const uint32_t *samples, const SeriesDesc *raw_desc, int64_t S, uint16_t *feat,
+                             cudaStream_t st);
 
 cudaError_t launch_reduce_rank(const uint32_t *samples, const SeriesDesc *raw_desc, int64_t S,
                                double *red, uint32_t *rank_out, cudaStream_t st);

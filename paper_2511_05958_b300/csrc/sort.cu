@@ -262,6 +262,8 @@ sort_series_kernel(const uint32_t *__restrict__ samples, SeriesDesc *__restrict_
     if (tid == 0) {
         rt[count] = N;
         desc[s].nruns = (int32_t)count;
+        const uint32_t km = fk[N / 2];
+        desc[s].median = comp ? km >> 16 : km;
     }
 }
 

@@ -1,0 +1,207 @@
+"""GPU parity of the learned-proposal kernels against the numpy oracle (oracle/cnn_oracle.py).
+
+Features are BF16 on both sides (at most one BF16 step apart where FP32 and FP64 logarithms
+round differently); logits and gradients are compared with a relative L2 tolerance of 1e-3 per
+tensor, from the same BF16 weights and features.
+"""
+import numpy as np
+import pytest
+
+import paper_2511_05958_b300 as mt4g
+import synth
+from oracle import cnn_oracle as C
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def eng():
+    import torch
+    assert torch.cuda.is_available()
+    e = mt4g.Engine(0)
+    yield e
+    e.close()
+
+
+def bf16_bits_to_float(t):
+    a = t.cpu().numpy().astype(np.int32) & 0xFFFF
+    return (a.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+def split_features(feat, steps):
+    """GPU feature rows -> list of [17, T] arrays."""
+    out, r = [], 0
+    for T in steps:
+        out.append(feat[r + 2:r + 2 + T, :17].T.copy())
+        r += T + 4
+    return out
+
+
+def flat_to_layers(w):
+    """Flat [d][i][o] weights -> oracle layers [(W[o][i][d], b)], dropping input channel 17."""
+    layers, off = [], 0
+    for cin_pad, cin, cout in [(18, 17, 32), (32, 32, 32), (32, 32, 32), (32, 32, 1)]:
+        n = 5 * cin_pad * cout
+        W = w[off:off + n].reshape(5, cin_pad, cout)[:, :cin, :].transpose(2, 1, 0).astype(np.float64)
+        off += n
+        b = w[off:off + cout].astype(np.float64)
+        off += cout
+        layers.append((W, b))
+    assert off == mt4g.CNN_PARAMS
+    return layers
+
+
+def layers_to_flat(grads):
+    parts = []
+    for (gW, gb), cin_pad in zip(grads, [18, 32, 32, 32]):
+        cout, cin, _ = gW.shape
+        full = np.zeros((5, cin_pad, cout))
+        full[:, :cin, :] = gW.transpose(2, 1, 0)
+        parts += [full.ravel(), gb.ravel()]
+    return np.concatenate(parts)
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def test_summaries_match_oracle(eng):
+    rng = np.random.default_rng(0)
+    series = [synth.generate(2, 5, 2).series(1)]
+    for m in (1, 8, 16, 33, 64, 100, 128, 256):
+        T = int(rng.integers(2, 80))
+        series.append(rng.integers(1, 3000, size=(T, m)).astype(np.uint32))
+    series.append(np.zeros((5, 4), np.uint32))  # values read as 1
+    b = synth.from_arrays(series)
+    feat = eng.summaries(mt4g.to_device_samples(b.samples), b.offsets, b.steps)
+    got = bf16_bits_to_float(feat)
+    # pad rows are zero
+    r = 0
+    for T in b.steps:
+        assert (got[r:r + 2] == 0).all() and (got[r + T + 2:r + T + 4] == 0).all()
+        assert (got[r + 2:r + 2 + T, 17] == 0).all()
+        r += T + 4
+    for x, g in zip(series, split_features(got, b.steps)):
+        ref = C.bf16(C.summaries(x))
+        ulp = np.maximum(np.abs(ref), 2.0 ** -126) * 2.0 ** -7
+        assert (np.abs(g - ref) <= ulp + 1e-30).all(), np.max(np.abs(g - ref))
+        assert np.mean(g == ref) > 0.99
+
+
+def _batch(eng, S=6, seed=3):
+    b = synth.generate(2, seed, S)
+    feat = eng.summaries(mt4g.to_device_samples(b.samples), b.offsets, b.steps)
+    return b, feat
+
+
+def test_forward_matches_oracle(eng):
+    b, feat = _batch(eng)
+    eng.cnn_init(7)
+    w = eng.cnn_get_params()
+    logits = eng.cnn_forward(feat, b.steps).cpu().numpy()
+    params = flat_to_layers(w)
+    xs = split_features(bf16_bits_to_float(feat), b.steps)
+    r = 0
+    for x, T in zip(xs, b.steps):
+        z, _ = C.forward(params, x, round_bf16=True)
+        g = logits[r + 2:r + 2 + T]
+        assert rel_l2(g, z) < 1e-3
+        r += T + 4
+
+
+def test_gradients_match_oracle(eng):
+    import torch
+    rng = np.random.default_rng(4)
+    b, feat = _batch(eng, S=8, seed=6)
+    eng.cnn_init(11)
+    w = eng.cnn_get_params()
+    # give biases non-zero values so every path is exercised
+    w[2880:2912] = rng.normal(size=32) * 0.1
+    eng.cnn_set_params(w)
+    max_cp = 4
+    cps = [list(b.cps[s, :3]) for s in range(8)]
+    cps[2] = []          # a series without a target is masked out
+    cps[5] = [7]
+    cnt = torch.tensor([len(c) for c in cps], dtype=torch.int32, device="cuda")
+    idx = torch.tensor([c + [-1] * (max_cp - len(c)) for c in cps], dtype=torch.int32, device="cuda")
+    grad, loss = eng.cnn_grads(feat, 512, 8, cnt, idx)
+    grad = grad.cpu().numpy().astype(np.float64)
+    params = flat_to_layers(w)
+    xs = split_features(bf16_bits_to_float(feat), b.steps)
+    ref_loss, ref_grads = C.loss_and_grads(params, xs, cps, round_bf16=True)
+    assert abs(float(loss.item()) - ref_loss) <= 1e-3 * abs(ref_loss)
+    ref = layers_to_flat(ref_grads)
+    off = 0
+    errs = []
+    for cin_pad, cout in [(18, 32), (32, 32), (32, 32), (32, 1)]:
+        n = 5 * cin_pad * cout
+        errs.append(rel_l2(grad[off:off + n], ref[off:off + n]))
+        off += n
+        if cout > 1:
+            errs.append(rel_l2(grad[off:off + cout], ref[off:off + cout]))
+        else:
+            # the output bias gets sum_t (p_t - y_t) = 0 exactly: check it is zero to rounding
+            assert abs(grad[off]) < 1e-5 and abs(ref[off]) < 1e-12
+        off += cout
+    assert max(errs) < 1e-3, errs
+    # the zero input channel gets no gradient
+    assert (grad[:2880].reshape(5, 18, 32)[:, 17, :] == 0).all()
+
+
+def test_adam_step_and_checkpoint_roundtrip(eng, tmp_path):
+    import torch
+    b, feat = _batch(eng, S=4, seed=8)
+    eng.cnn_init(5)
+    w0 = eng.cnn_get_params().astype(np.float64)
+    cnt = torch.tensor([3, 3, 3, 3], dtype=torch.int32, device="cuda")
+    idx = torch.tensor(b.cps[:, :3], dtype=torch.int32, device="cuda").contiguous()
+    g, _ = eng.cnn_grads(feat, 512, 4, cnt, idx)
+    g = g.cpu().numpy().astype(np.float64)
+    eng.cnn_train_step(feat, 512, 4, cnt, idx, lr=1e-3)
+    w1 = eng.cnn_get_params().astype(np.float64)
+    m, v = {}, {}
+    exp = C.adam_step([(w0, np.zeros(1))], [(g, np.zeros(1))], m, v, step=1)[0][0]
+    assert np.allclose(w1, exp, rtol=1e-5, atol=1e-7)
+    path = str(tmp_path / "w.bin")
+    eng.cnn_save(path)
+    eng.cnn_init(99)
+    eng.cnn_load(path)
+    assert np.array_equal(eng.cnn_get_params().astype(np.float64), w1)
+    raw = bytearray(open(path, "rb").read())
+    raw[100] ^= 0xFF
+    open(path, "wb").write(bytes(raw))
+    with pytest.raises(mt4g.Mt4gError) as e:
+        eng.cnn_load(path)
+    assert e.value.code == mt4g.EINVAL
+
+
+def test_propose_matches_oracle_windows(eng):
+    b, feat = _batch(eng, S=16, seed=9)
+    eng.cnn_init(3)
+    d = mt4g.to_device_samples(b.samples)
+    win, conf = eng.propose(d, b.offsets, b.steps, 3, 16)
+    logits = eng.cnn_forward(feat, b.steps).cpu().numpy()
+    win = win.cpu().numpy()
+    conf = conf.cpu().numpy()
+    r = 0
+    for s, T in enumerate(b.steps):
+        z = logits[r + 2:r + 2 + T].astype(np.float64)
+        centres, c = C.propose(z, 3, 16)
+        assert list(win[s]) == centres
+        assert abs(conf[s] - c) < 1e-4
+        r += T + 4
+
+
+def test_training_reduces_loss(eng):
+    """A few hundred steps on one batch overfit it: the loss must drop."""
+    import torch
+    b, feat = _batch(eng, S=32, seed=12)
+    eng.cnn_init(1)
+    cnt = torch.full((32,), 3, dtype=torch.int32, device="cuda")
+    idx = torch.tensor(b.cps[:, :3], dtype=torch.int32, device="cuda").contiguous()
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    _, l0 = eng.cnn_grads(feat, 512, 32, cnt, idx)
+    for _ in range(300):
+        eng.cnn_train_step(feat, 512, 32, cnt, idx, lr=3e-3, loss=loss)
+    _, l1 = eng.cnn_grads(feat, 512, 32, cnt, idx)
+    assert float(l1.item()) < 0.5 * float(l0.item())
