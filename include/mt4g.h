@@ -56,6 +56,7 @@ extern "C" {
 #define MT4G_ETIMEOUT (-5)  /* a bounded device-side wait expired; outputs are incomplete */
 
 #define MT4G_MODE_FULL 0    /* every split of every segment is evaluated */
+#define MT4G_MODE_LEARNED 1 /* proposal windows + exact certification; same answers as FULL */
 #define MT4G_MODE_REDUCED 2 /* Eq. 2 reduction first: one FP64 value per step, then the same test */
 
 #define MT4G_MAX_STEPS 32768
@@ -66,6 +67,10 @@ extern "C" {
 #define MT4G_OPT_STAGE_TIMING 2  /* 1: record CUDA events between the stages of every call */
 #define MT4G_OPT_SCAN_KPT 3      /* scan tile: 0 = per-series choice (default), else 1, 2 or 4
                                     groups of 32 splits per warp work item for every series */
+#define MT4G_OPT_WINDOWS 4       /* learned mode: proposal windows per series (default 3) */
+#define MT4G_OPT_HALF_WIDTH 5    /* learned mode: window half width in steps (default 16) */
+#define MT4G_OPT_CONF_MIN_PPM 6  /* learned mode: series whose window mass is below this (in
+                                    millionths, default 900000) take the full scan */
 
 typedef struct mt4g_ctx mt4g_ctx;
 
@@ -112,12 +117,20 @@ int mt4g_ks_scan(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets,
  * first min(count, max_cp) change points of series s in ascending order, each
  * with the D and p of the split that created it; unused slots are -1, 0, 0, 1.0.
  * If some count exceeds max_cp, mt4g_wait() returns MT4G_ECAPACITY.
- * mode: MT4G_MODE_FULL or MT4G_MODE_REDUCED (as in mt4g_ks_scan).
+ * mode: MT4G_MODE_FULL or MT4G_MODE_REDUCED (as in mt4g_ks_scan), or MT4G_MODE_LEARNED:
+ *   the proposal network (weights from mt4g_cnn_load / mt4g_cnn_init; m <= 256) gives
+ *   each series windows and a confidence (mt4g_propose).  Series below the confidence
+ *   threshold take the full scan.  For the others every segment is first scanned exactly
+ *   at the windows' splits and at up to 32 grid splits; each gap between grid splits gets
+ *   a bound on D from its two end columns, and the gaps whose bound might reach the best
+ *   D found are scanned exactly.  The results are therefore those of MT4G_MODE_FULL.
+ * fallback: DEVICE int32 [S] or NULL; 1 where the series took the full scan (always 0
+ *   outside learned mode).
  */
 int mt4g_ks_segment(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets, const int32_t *steps,
                     int64_t S, double alpha, int32_t min_seg, int32_t max_cp, int32_t mode,
                     int32_t *cp_count, int32_t *cp_idx, int64_t *dnum, int64_t *dden, double *p,
-                    void *cuda_stream);
+                    int32_t *fallback, void *cuda_stream);
 
 /* ------------------------------------------------------------------ learned proposal
  *
@@ -200,6 +213,9 @@ int mt4g_propose(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets,
  */
 int mt4g_stage_times(mt4g_ctx *ctx, double *ms_out, int32_t max_calls);
 int mt4g_last_work(mt4g_ctx *ctx, int64_t *evals);
+/* After mt4g_wait() on a learned call: out[0] = segments decided by their probe group,
+ * out[1] = segments that needed refinement slices, out[2] = probe groups pushed. */
+int mt4g_learned_stats(mt4g_ctx *ctx, int64_t *out);
 
 #ifdef __cplusplus
 }

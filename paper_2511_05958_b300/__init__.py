@@ -17,10 +17,13 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmt4g.so")
 
 OK, EINVAL, ECAPACITY, ENOMEM, ECUDA, ETIMEOUT = 0, -1, -2, -3, -4, -5
-MODE_FULL, MODE_REDUCED = 0, 2
+MODE_FULL, MODE_LEARNED, MODE_REDUCED = 0, 1, 2
 OPT_WAIT_LIMIT_NS = 1
 OPT_STAGE_TIMING = 2
 OPT_SCAN_KPT = 3
+OPT_WINDOWS = 4
+OPT_HALF_WIDTH = 5
+OPT_CONF_MIN_PPM = 6
 MAX_STEPS = 32768
 FEAT_CHANNELS = 18
 CNN_PARAMS = 13377
@@ -57,7 +60,8 @@ def load_library():
     L.mt4g_wait.argtypes = [vp]
     L.mt4g_set_option.argtypes = [vp, ctypes.c_int, i64]
     L.mt4g_ks_scan.argtypes = [vp, vp, vp, vp, i64, i32, vp, vp, vp, vp, vp]
-    L.mt4g_ks_segment.argtypes = [vp, vp, vp, vp, i64, dbl, i32, i32, i32, vp, vp, vp, vp, vp, vp]
+    L.mt4g_ks_segment.argtypes = [vp, vp, vp, vp, i64, dbl, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp]
+    L.mt4g_learned_stats.argtypes = [vp, vp]
     L.mt4g_stage_times.argtypes = [vp, vp, i32]
     L.mt4g_last_work.argtypes = [vp, vp]
     L.mt4g_summaries.argtypes = [vp, vp, vp, vp, i64, vp, vp]
@@ -79,7 +83,8 @@ def exported_symbols():
     return ["mt4g_create", "mt4g_destroy", "mt4g_last_error", "mt4g_wait", "mt4g_set_option",
             "mt4g_ks_scan", "mt4g_ks_segment", "mt4g_stage_times", "mt4g_last_work",
             "mt4g_summaries", "mt4g_cnn_init", "mt4g_cnn_get_params", "mt4g_cnn_set_params", "mt4g_cnn_save",
-            "mt4g_cnn_load", "mt4g_cnn_forward", "mt4g_cnn_grads", "mt4g_cnn_train_step", "mt4g_propose"]
+            "mt4g_cnn_load", "mt4g_cnn_forward", "mt4g_cnn_grads", "mt4g_cnn_train_step", "mt4g_propose",
+            "mt4g_learned_stats"]
 
 
 class ScanResult(NamedTuple):
@@ -96,6 +101,7 @@ class SegmentResult(NamedTuple):
     dnum: "torch.Tensor"
     dden: "torch.Tensor"
     p: "torch.Tensor"
+    fallback: "torch.Tensor"  # [S], 1 where a learned call took the full scan
 
 
 def _host_tables(offsets, steps):
@@ -170,6 +176,12 @@ class Engine:
             self._check(n)
         return buf[:n]
 
+    def learned_stats(self) -> dict:
+        """Certification counters of the last learned call (valid after wait())."""
+        v = np.zeros(3, np.int64)
+        self._check(self._L.mt4g_learned_stats(self._h, v.ctypes.data_as(ctypes.c_void_p)))
+        return {"certified": int(v[0]), "refined": int(v[1]), "probe_groups": int(v[2])}
+
     def last_work(self) -> int:
         """(split, distinct value) pairs evaluated by the last call (valid after wait())."""
         v = np.zeros(1, np.int64)
@@ -205,12 +217,13 @@ class Engine:
                                 torch.empty((S, max_cp), dtype=torch.int32, device=dev),
                                 torch.empty((S, max_cp), dtype=torch.int64, device=dev),
                                 torch.empty((S, max_cp), dtype=torch.int64, device=dev),
-                                torch.empty((S, max_cp), dtype=torch.float64, device=dev))
+                                torch.empty((S, max_cp), dtype=torch.float64, device=dev),
+                                torch.empty(S, dtype=torch.int32, device=dev))
         rc = self._L.mt4g_ks_segment(self._h, _dev_ptr(samples, "samples"), offsets.ctypes.data_as(ctypes.c_void_p),
                                      steps.ctypes.data_as(ctypes.c_void_p), S, float(alpha), int(min_seg),
                                      int(max_cp), mode, _dev_ptr(out.count, "count"), _dev_ptr(out.idx, "idx"),
                                      _dev_ptr(out.dnum, "dnum"), _dev_ptr(out.dden, "dden"), _dev_ptr(out.p, "p"),
-                                     _stream_handle(stream))
+                                     _dev_ptr(out.fallback, "fallback"), _stream_handle(stream))
         self._check(rc)
         status = OK
         if sync:

@@ -31,6 +31,10 @@ struct mt4g_ctx {
     bool last_enqueued = false;  // the most recent call enqueued work (its status is in h_hdr)
 
     int32_t forced_kpt = 0;  // 0: per-series choice; 1, 2, 4: every series
+    int32_t n_win = 3;       // learned proposals: windows per series
+    int32_t half = 16;       // window half width
+    float conf_min = 0.9f;   // below: the series takes the plain scan
+    float *learned_conf = nullptr;  // device: proposal confidence of the last learned call
 
     // proposal network
     CnnState cnn;
@@ -103,6 +107,8 @@ struct Plan {
     std::vector<int64_t> item_base;    // first queue slot of the top-level slices of qorder[i]
     int64_t n_init = 0;                // top-level slices
     unsigned long long cap = 0;
+    bool learned = false;              // items are pushed by the learned init kernel
+    unsigned long long rec_cap = 0;    // certification records (learned mode)
 };
 
 struct Buffers {
@@ -120,6 +126,9 @@ struct Buffers {
     double *cp_p;
     WorkItem *items;
     int32_t *ready;
+    uint32_t *gcount;
+    CertRecord *recs;
+    int32_t *fallback;
     double *red;
     uint32_t *rank;
 };
@@ -143,6 +152,9 @@ size_t carve(void *base, const Plan &P, Buffers &B, size_t *ready_off) {
     B.cp_p = c.take<double>(P.sumT);
     B.red = c.take<double>(P.reduced ? P.sumT : 0);
     B.rank = c.take<uint32_t>(P.reduced ? P.sumT : 0);
+    B.gcount = c.take<uint32_t>(P.cap);
+    B.recs = c.take<CertRecord>(P.learned ? P.rec_cap : 0);
+    B.fallback = c.take<int32_t>(P.S);
     B.items = c.take<WorkItem>(P.cap);
     B.ready = c.take<int32_t>(P.cap);
     *ready_off = (size_t)((char *)B.ready - (char *)base);
@@ -169,8 +181,8 @@ int make_plan(mt4g_ctx *ctx, const int64_t *offsets, const int32_t *steps, int64
     if (S < 0) return fail(ctx, MT4G_EINVAL, "S must be >= 0 (got %lld)", (long long)S);
     if (S > 0 && (!offsets || !steps)) return fail(ctx, MT4G_EINVAL, "offsets and steps must be non-NULL");
     if (S > (int64_t)INT32_MAX) return fail(ctx, MT4G_EINVAL, "too many series");
-    if (mode != MT4G_MODE_FULL && mode != MT4G_MODE_REDUCED)
-        return fail(ctx, MT4G_EINVAL, "mode must be MT4G_MODE_FULL or MT4G_MODE_REDUCED (got %d)", mode);
+    if (mode != MT4G_MODE_FULL && mode != MT4G_MODE_REDUCED && mode != MT4G_MODE_LEARNED)
+        return fail(ctx, MT4G_EINVAL, "mode must be MT4G_MODE_FULL, _REDUCED or _LEARNED (got %d)", mode);
     if (min_seg < 1) return fail(ctx, MT4G_EINVAL, "min_seg must be >= 1 (got %d)", min_seg);
     if (S > 0 && offsets[0] != 0) return fail(ctx, MT4G_EINVAL, "offsets[0] must be 0");
     P.S = S;
@@ -246,6 +258,12 @@ int make_plan(mt4g_ctx *ctx, const int64_t *offsets, const int32_t *steps, int64
     // two slices beyond the parent's, so 2 per step plus the top level bounds them
     // for the usual few change points per series; overflow is reported.
     P.cap = (unsigned long long)nb + 4ull * (unsigned long long)sumT + 1024ull;
+    P.learned = mode == MT4G_MODE_LEARNED;
+    if (P.learned) {
+        // probe groups (windows + grid) and refinements come on top of the plain slices
+        P.cap += 8ull * (unsigned long long)S + 2ull * (unsigned long long)sumT;
+        P.rec_cap = 16ull * (unsigned long long)S + 1024ull;
+    }
     return MT4G_OK;
 }
 
@@ -310,10 +328,11 @@ int enqueue_pipeline(mt4g_ctx *ctx, const uint32_t *samples, Plan &P, RunParams 
     char *h = (char *)ctx->pin;
     QueueHeader hq{};
     hq.head = 0;
-    hq.tail = n_items;
-    hq.pending = (long long)n_items;
+    hq.tail = P.learned ? 0 : n_items;
+    hq.pending = P.learned ? 0 : (long long)n_items;
     hq.status = 0;
     hq.cap = P.cap;
+    hq.rec_cap = P.rec_cap;
     size_t o = 0;
     memcpy(h + o, &hq, bytes_hdr);
     o += bytes_hdr;
@@ -341,7 +360,9 @@ int enqueue_pipeline(mt4g_ctx *ctx, const uint32_t *samples, Plan &P, RunParams 
     if (bytes_ready)
         CUDA_TRY(ctx, cudaMemcpyAsync(B.item_base, h + o_ready, bytes_ready, cudaMemcpyHostToDevice, st));
     CUDA_TRY(ctx, cudaEventRecord(ctx->pin_free, st));
-    CUDA_TRY(ctx, launch_init_items(B.desc, B.qorder, B.item_base, P.S, P.min_seg, B.items, B.ready, epoch, st));
+    if (!P.learned)
+        CUDA_TRY(ctx, launch_init_items(B.desc, B.qorder, B.item_base, P.S, P.min_seg, B.items, B.ready, B.gcount,
+                                        epoch, st));
     mark(ctx, 1, st);
 
     const uint32_t *sort_in = samples;
@@ -359,6 +380,9 @@ int enqueue_pipeline(mt4g_ctx *ctx, const uint32_t *samples, Plan &P, RunParams 
     R.q = B.q;
     R.items = B.items;
     R.ready = B.ready;
+    R.gcount = B.gcount;
+    R.recs = B.recs;
+    R.fallback = B.fallback;
     R.min_seg = P.min_seg;
     R.wait_limit_ns = ctx->wait_limit_ns;
     R.cp_flag = B.cp_flag;
@@ -367,6 +391,8 @@ int enqueue_pipeline(mt4g_ctx *ctx, const uint32_t *samples, Plan &P, RunParams 
     R.cp_p = B.cp_p;
     return (int)epoch;  // >= 0
 }
+
+int enqueue_proposals(mt4g_ctx *ctx, const uint32_t *samples, Plan &P, Buffers &B, RunParams &R, cudaStream_t st);
 
 int finish_call(mt4g_ctx *ctx, Buffers &B, cudaStream_t st) {
     mark(ctx, 4, st);
@@ -457,6 +483,21 @@ int mt4g_set_option(mt4g_ctx *c, int option, int64_t value) {
         c->forced_kpt = (int32_t)value;
         return MT4G_OK;
     }
+    if (option == MT4G_OPT_WINDOWS) {
+        if (value < 1 || value > 8) return fail(c, MT4G_EINVAL, "windows must be 1..8");
+        c->n_win = (int32_t)value;
+        return MT4G_OK;
+    }
+    if (option == MT4G_OPT_HALF_WIDTH) {
+        if (value < 0 || value > 31) return fail(c, MT4G_EINVAL, "half width must be 0..31");
+        c->half = (int32_t)value;
+        return MT4G_OK;
+    }
+    if (option == MT4G_OPT_CONF_MIN_PPM) {
+        if (value < 0 || value > 1000001) return fail(c, MT4G_EINVAL, "confidence threshold must be 0..1000001 ppm");
+        c->conf_min = (float)((double)value * 1e-6);
+        return MT4G_OK;
+    }
     if (option == MT4G_OPT_WAIT_LIMIT_NS) {
         if (value <= 0) return fail(c, MT4G_EINVAL, "wait limit must be > 0 ns");
         c->wait_limit_ns = value;
@@ -507,16 +548,22 @@ int mt4g_ks_scan(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets,
 
 int mt4g_ks_segment(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets, const int32_t *steps, int64_t S,
                     double alpha, int32_t min_seg, int32_t max_cp, int32_t mode, int32_t *cp_count, int32_t *cp_idx,
-                    int64_t *dnum, int64_t *dden, double *p, void *cuda_stream) {
+                    int64_t *dnum, int64_t *dden, double *p, int32_t *fallback, void *cuda_stream) {
     int rc = begin_call(ctx);
     if (rc) return rc;
     if (!(alpha > 0.0 && alpha < 1.0)) return fail(ctx, MT4G_EINVAL, "alpha must be in (0, 1)");
     if (max_cp < 0) return fail(ctx, MT4G_EINVAL, "max_cp must be >= 0");
     if (S > 0 && (!samples || !cp_count || (max_cp > 0 && (!cp_idx || !dnum || !dden || !p))))
         return fail(ctx, MT4G_EINVAL, "NULL device pointer");
+    if (mode == MT4G_MODE_LEARNED && !ctx->cnn_ready)
+        return fail(ctx, MT4G_EINVAL, "learned mode needs weights: call mt4g_cnn_load or mt4g_cnn_init");
     Plan P;
     rc = make_plan(ctx, offsets, steps, S, mode, min_seg, P);
     if (rc) return rc;
+    if (mode == MT4G_MODE_LEARNED)
+        for (int64_t s = 0; s < S; s++)
+            if (P.desc[s].m > 256)
+                return fail(ctx, MT4G_EINVAL, "series %lld: learned mode needs m <= 256", (long long)s);
     if (S == 0) return MT4G_OK;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     Buffers B;
@@ -524,13 +571,22 @@ int mt4g_ks_segment(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offse
     mark(ctx, 0, st);
     const int epoch = enqueue_pipeline(ctx, samples, P, R, B, st);
     if (epoch < 0) return epoch;
-    R.mode = kRunSegment;
+    R.mode = P.learned ? kRunLearned : kRunSegment;
     R.alpha = alpha;
     CUDA_TRY(ctx, cudaMemsetAsync(B.cp_flag, 0, (size_t)P.sumT, st));
+    if (P.learned) {
+        rc = enqueue_proposals(ctx, samples, P, B, R, st);
+        if (rc) return rc;
+        CUDA_TRY(ctx, launch_init_learned(R, ctx->learned_conf, ctx->conf_min, B.fallback, P.S, (uint32_t)epoch, st));
+    } else {
+        CUDA_TRY(ctx, cudaMemsetAsync(B.fallback, 0, P.S * sizeof(int32_t), st));
+    }
     CUDA_TRY(ctx, launch_queue_run(R, ctx->grid, (uint32_t)epoch, st));
     mark(ctx, 3, st);
     CUDA_TRY(ctx, launch_collect(B.desc, P.S, B.cp_flag, B.cp_num, B.cp_den, B.cp_p, max_cp, cp_count, cp_idx, dnum,
                                  dden, p, B.q, st));
+    if (fallback)
+        CUDA_TRY(ctx, cudaMemcpyAsync(fallback, B.fallback, P.S * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
     return finish_call(ctx, B, st);
 }
 
@@ -948,3 +1004,41 @@ int mt4g_propose(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets,
 }
 
 }  // extern "C"
+
+namespace {
+
+// Learned mode: features, logits and windows of every series (after the sort has written
+// the medians), for the learned init kernel and the probe groups.
+int enqueue_proposals(mt4g_ctx *ctx, const uint32_t *samples, Plan &P, Buffers &B, RunParams &R, cudaStream_t st) {
+    const int64_t S = P.S;
+    const int64_t rows = P.sumT + 4 * S;
+    CnnBuffers C;
+    const size_t need = carve_cnn(nullptr, rows, S, false, true, ctx->n_win, C);
+    int rc = ensure_cnn_ws(ctx, need);
+    if (rc) return rc;
+    carve_cnn(ctx->cnn_ws, rows, S, false, true, ctx->n_win, C);
+    int64_t ntiles = 0;
+    rc = upload_cnn_tables(ctx, P.desc, C, &ntiles, st);
+    if (rc) return rc;
+    rc = zero_pads(ctx, C, S, false, st);
+    if (rc) return rc;
+    CUDA_TRY(ctx, launch_summaries(samples, B.desc, S, C.feat, st));
+    CUDA_TRY(ctx, cnn_prepare(ctx->cnn, st));
+    CUDA_TRY(ctx, cnn_forward(ctx->cnn, C.feat, C.A, B.desc, C.tiles_before, S, ntiles, st));
+    CUDA_TRY(ctx, launch_propose(C.A.logits, B.desc, S, ctx->n_win, ctx->half, C.win, C.conf, st));
+    R.win_center = C.win;
+    R.n_win = ctx->n_win;
+    R.half = ctx->half;
+    ctx->learned_conf = C.conf;
+    return MT4G_OK;
+}
+
+}  // namespace
+
+extern "C" int mt4g_learned_stats(mt4g_ctx *c, int64_t *out) {
+    if (!c || !out) return MT4G_EINVAL;
+    out[0] = (int64_t)c->h_hdr->certified;
+    out[1] = (int64_t)c->h_hdr->refined;
+    out[2] = (int64_t)c->h_hdr->rec_next;
+    return MT4G_OK;
+}

@@ -8,7 +8,7 @@
 //   runs       int32[Ntot + S]  per series: start of each run of equal values,
 //                               runs[run_base + j], j in [0, U_s], last = N_s
 //   cp_flag/num/den/p [sum T]   per step: a change point accepted at that step
-//   queue      WorkItem[cap] + ready[cap]   the device work queue
+//   queue      WorkItem[cap] + ready[cap] + gcount[cap]   the device work queue
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -42,17 +42,39 @@ struct SeriesDesc {
 constexpr int kFeatC = 18;  // 16 quantiles + step size + one zero channel
 __host__ __device__ inline int64_t row_base(const SeriesDesc &d, int64_t s) { return d.step_base + 4 * s; }
 
-// One unit of work: the splits of slice `chunk` of segment [lo, hi) of a series.
-// With w = 32 kpt splits per slice, slice c covers k in [lo + min_seg + w c, ... + w - 1],
-// up to hi - min_seg.
+// One unit of work on segment [lo, hi) of a series, member `chunk` of a group of
+// `nch` items pushed together; the last member to finish combines the group.
+//   kPlain:  splits [lo + min_seg + w c, ... + w - 1] with w = 32 kpt, c = chunk
+//   kWindow: the 32 splits from k0 (a proposal window), exact
+//   kGrid:   exact columns at up to 32 grid splits and bounds over the gaps between them
+//   kRefine: the 32 splits from k0, up to klim, inside a gap that was not certified
+// Splits outside [lo + min_seg, hi - min_seg] are never evaluated.
+enum ItemKind : int32_t { kPlain = 0, kWindow = 1, kGrid = 2, kRefine = 3 };
 struct WorkItem {
     int32_t series;
     int32_t lo;
     int32_t hi;
     int32_t chunk;
+    int32_t kind_nch;  // kind | nch << 8
+    int32_t k0;
+    int32_t klim;
+    int32_t rec;       // certification record of the segment (learned groups), else -1
+};
+__host__ __device__ inline int32_t item_kind(const WorkItem &w) { return w.kind_nch & 0xff; }
+__host__ __device__ inline int32_t item_nch(const WorkItem &w) { return w.kind_nch >> 8; }
+
+// Certification record of one learned segment: the grid's gaps and the best exact split.
+constexpr int kMaxGrid = 32;
+struct CertRecord {
+    int32_t best_k;
+    int32_t n_gap;
+    uint64_t best_g;
+    int32_t a[kMaxGrid - 1];  // gap j covers splits a[j] < k < b[j]
+    int32_t b[kMaxGrid - 1];
+    uint64_t ub[kMaxGrid - 1];  // bound on max_x |H c_L - (k - lo) C| for a[j] <= k <= b[j]
 };
 
-// Partial result of one chunk, written over its (already consumed) queue slot.
+// Partial result of one group member, written over its (already consumed) queue slot.
 struct ChunkResult {
     int32_t k;
     int32_t pad;
@@ -69,9 +91,13 @@ struct QueueHeader {
     int32_t pad;
     unsigned long long cap;      // slots
     unsigned long long evals;    // (k, distinct value) pairs evaluated
+    unsigned long long rec_next; // certification records handed out
+    unsigned long long rec_cap;
+    unsigned long long refined;  // learned segments that needed refinement slices
+    unsigned long long certified;  // learned segments decided by their probe group
 };
 
-enum RunMode : int32_t { kRunScan = 0, kRunSegment = 1 };
+enum RunMode : int32_t { kRunScan = 0, kRunSegment = 1, kRunLearned = 2 };
 
 struct RunParams {
     const SeriesDesc *desc;
@@ -80,6 +106,7 @@ struct RunParams {
     QueueHeader *q;
     WorkItem *items;
     int32_t *ready;
+    uint32_t *gcount;      // per group (at its first slot): members finished
     int32_t mode;          // kRunScan / kRunSegment
     int32_t min_seg;
     double alpha;
@@ -94,6 +121,12 @@ struct RunParams {
     int64_t *cp_num;
     int64_t *cp_den;
     double *cp_p;
+    // learned segmentation
+    const int32_t *win_center;  // [S * n_win], -1 = none
+    int32_t n_win;
+    int32_t half;               // window slice covers [c - half, c - half + 31]
+    const int32_t *fallback;    // [S]: 1 = the series takes the plain path
+    CertRecord *recs;
 };
 
 // Number of slices of a segment of H steps (0 if it cannot be split).
@@ -110,7 +143,10 @@ cudaError_t launch_sort(const uint32_t *samples, SeriesDesc *desc, const int32_t
 
 cudaError_t launch_queue_run(const RunParams &P, int grid, uint32_t epoch, cudaStream_t st);
 cudaError_t launch_init_items(const SeriesDesc *desc, const int32_t *qorder, const int64_t *item_base, int64_t S,
-                              int32_t min_seg, WorkItem *items, int32_t *ready, uint32_t epoch, cudaStream_t st);
+                              int32_t min_seg, WorkItem *items, int32_t *ready, uint32_t *gcount, uint32_t epoch,
+                              cudaStream_t st);
+cudaError_t launch_init_learned(const RunParams &P, const float *conf, float conf_min, int32_t *fallback_out,
+                                int64_t S, uint32_t epoch, cudaStream_t st);
 int queue_grid(int device);
 
 cudaError_t launch_collect(const SeriesDesc *desc, int64_t S, const uint8_t *cp_flag, const int64_t *cp_num,

@@ -23,11 +23,12 @@
 // products and sums are explicit round-to-nearest operations so the result is the
 // same IEEE sequence a plain C evaluation performs.
 //
-// Work queue: an item is (series, lo, hi, chunk), the 32 splits of one slice of a
-// segment, scanned by one warp.  A warp takes a ticket, waits (bounded, on the global
-// timer) until that slot is published or no work is pending, scans, and the last slice
-// of a segment to finish combines the slices' results, computes p and, if p <= alpha,
-// records the change point and publishes the slices of the two children.
+// Work queue: an item is one member of a group pushed together for a segment (the
+// slices of a full scan, or a learned probe / refinement group), processed by one warp.
+// A warp takes a ticket, waits (bounded, on the global timer) until that slot is
+// published or no work is pending, processes it, writes its best split over its slot and
+// counts itself done in the group's counter; the last member combines the group,
+// computes p and, if p <= alpha, records the change point and pushes the children.
 #include <climits>
 
 #include "mt4g_internal.cuh"
@@ -260,6 +261,64 @@ __device__ void scan_slice(const uint16_t *__restrict__ lab, const int32_t *__re
     for (int q = 0; q < KPT; q++) g[q] = WIDE ? mx[q] : (uint64_t)mx32[q];
 }
 
+// ---------------------------------------------------------------- grid columns and gap bounds
+
+// Exact columns at this lane's grid split gk (gk < 0: inactive lane) and, with the next
+// lane's split gn, a bound over the gap: for every split k in [gk, gn] and every x,
+//   H c_L^gk(x) - (gn - lo) C(x)  <=  H c_L^k(x) - (k - lo) C(x)  <=  H c_L^gn(x) - (gk - lo) C(x),
+// because c_L^k grows with k.  So |H c_L^k - (k - lo) C| is at most the larger modulus of
+// the two ends, and its maximum over x bounds g_k for the whole gap.
+__device__ __noinline__ void scan_grid(const uint16_t *__restrict__ lab, const int32_t *__restrict__ rt, int U, int T, int lo,
+                          int hi, int gk, int gn, SliceStage<1> &st, uint64_t &g_out, uint64_t &ub_out,
+                          int &nonempty) {
+    const int lane = threadIdx.x & 31;
+    const int64_t H = hi - lo;
+    const int64_t a = gk - lo, an = gn - lo;
+    int64_t cl = 0, C = 0;
+    uint64_t mx = 0, ub = 0;
+    nonempty = 0;
+    for (int j0 = 0; j0 < U; j0 += 32) {
+        const int j = j0 + lane;
+        int si = 0, ei = 0, fi = 0, la = 0;
+        if (j < U) {
+            const int a0 = __ldg(rt + j), b0 = __ldg(rt + j + 1);
+            const int f0 = __ldg(lab + a0), l0 = __ldg(lab + b0 - 1);
+            si = (f0 >= lo) ? a0 : (l0 < lo ? b0 : lower_bound_lab(lab, a0, b0, lo));
+            ei = (l0 < hi) ? b0 : (f0 >= hi ? a0 : lower_bound_lab(lab, si, b0, hi));
+            if (ei > si) {
+                fi = (si == a0) ? f0 : __ldg(lab + si);
+                la = (ei == b0) ? l0 : __ldg(lab + ei - 1);
+            }
+        }
+        const unsigned ne = __ballot_sync(kFull, ei > si);
+        if (ei > si) {
+            const int pos = __popc(ne & lanemask_lt());
+            st.si[pos] = si;
+            st.ei[pos] = ei;
+            st.cb[0][pos] = fi;
+            st.cb[1][pos] = la;
+        }
+        __syncwarp();
+        const int cnt = __popc(ne);
+        for (int r = 0; r < cnt; r++) {
+            const int rsi = st.si[r], rei = st.ei[r];
+            C += rei - rsi;
+            if (gk >= 0) cl += count_below(lab, rsi, rei, st.cb[0][r], st.cb[1][r], rsi, gk) - rsi;
+            const int64_t cn = __shfl_down_sync(kFull, cl, 1);
+            const int64_t f = H * cl - a * C;
+            const uint64_t af = (uint64_t)(f < 0 ? -f : f);
+            mx = af > mx ? af : mx;
+            const int64_t u1 = H * cn - a * C, u2 = H * cl - an * C;
+            const uint64_t au = max((uint64_t)(u1 < 0 ? -u1 : u1), (uint64_t)(u2 < 0 ? -u2 : u2));
+            ub = au > ub ? au : ub;
+        }
+        nonempty += cnt;
+        __syncwarp();
+    }
+    g_out = mx;
+    ub_out = ub;
+}
+
 // ---------------------------------------------------------------- queue helpers
 
 // Warp-wide argmax of D (ties to the smallest k); every lane ends with the result.
@@ -275,9 +334,77 @@ __device__ __forceinline__ void warp_best(int &bk, uint64_t &bg, int lo, int hi)
     }
 }
 
-// Decide a finished segment (all lanes call with the same arguments): p-value, outputs,
-// and if significant the change point and the children's slices.
-__device__ void finish_segment(const RunParams &P, const SeriesDesc &d, int series, int lo, int hi, int k,
+// Reserve `tot` queue slots and count them as pending (one lane).  Returns the first slot,
+// or ~0 when the queue is full (then nothing is pending and the status says so).
+__device__ unsigned long long reserve_slots(const RunParams &P, int tot) {
+    atomicAdd((unsigned long long *)&P.q->pending, (unsigned long long)tot);
+    const unsigned long long base = atomicAdd(&P.q->tail, (unsigned long long)tot);
+    if (base + tot > P.q->cap) {
+        atomicOr(&P.q->status, kStatusQueueFull);
+        atomicAdd((unsigned long long *)&P.q->pending, (unsigned long long)(-(long long)tot));
+        return ~0ull;
+    }
+    return base;
+}
+
+__device__ __forceinline__ void put_item(const RunParams &P, unsigned long long slot, const WorkItem &w) {
+    int4 *dst = reinterpret_cast<int4 *>(P.items + slot);
+    dst[0] = make_int4(w.series, w.lo, w.hi, w.chunk);
+    dst[1] = make_int4(w.kind_nch, w.k0, w.klim, w.rec);
+}
+
+// Push the work for segment [lo, hi) (all lanes of a warp call it with the same arguments).
+// Plain series: the slices of the full scan.  Learned series: a probe group of the window
+// slices that reach the segment's splits plus one grid item.
+__device__ __noinline__ void push_segment(const RunParams &P, const SeriesDesc &d, int series, int lo, int hi, uint32_t epoch) {
+    const int lane = threadIdx.x & 31;
+    const int A = lo + P.min_seg, B = hi - P.min_seg;
+    if (B < A) return;
+    const bool learned = P.mode == kRunLearned && !P.fallback[series];
+    if (!learned) {
+        const int nch = seg_chunks(hi - lo, P.min_seg, d.kpt);
+        unsigned long long base = 0;
+        if (lane == 0) base = reserve_slots(P, nch);
+        base = __shfl_sync(kFull, base, 0);
+        if (base == ~0ull) return;
+        for (int c = lane; c < nch; c += 32)
+            put_item(P, base + c, WorkItem{series, lo, hi, c, kPlain | (nch << 8), 0, B, -1});
+        if (lane == 0) P.gcount[base] = 0;
+        __threadfence();
+        for (int c = lane; c < nch; c += 32) st_release_u32((uint32_t *)P.ready + base + c, epoch);
+        return;
+    }
+    if (lane == 0) {
+        int ks[8];
+        int nw = 0;
+        for (int w = 0; w < P.n_win; w++) {
+            const int c = P.win_center[(int64_t)series * P.n_win + w];
+            if (c < 0) continue;
+            const int k0 = c - P.half;
+            if (k0 + 31 < A || k0 > B) continue;
+            ks[nw++] = k0;
+        }
+        const int tot = nw + 1;
+        const unsigned long long rec = atomicAdd(&P.q->rec_next, 1ull);
+        if (rec >= P.q->rec_cap) {
+            atomicOr(&P.q->status, kStatusQueueFull);
+            return;
+        }
+        const unsigned long long base = reserve_slots(P, tot);
+        if (base == ~0ull) return;
+        for (int j = 0; j < nw; j++)
+            put_item(P, base + j, WorkItem{series, lo, hi, j, kWindow | (tot << 8), ks[j], B, (int)rec});
+        put_item(P, base + nw, WorkItem{series, lo, hi, nw, kGrid | (tot << 8), A, B, (int)rec});
+        P.gcount[base] = 0;
+        __threadfence();
+        for (int j = 0; j < tot; j++) st_release_u32((uint32_t *)P.ready + base + j, epoch);
+    }
+    __syncwarp();
+}
+
+// Decide a segment whose best split is known exactly (all lanes, same arguments):
+// p-value, outputs, and if significant the change point and the work for both parts.
+__device__ __noinline__ void finish_segment(const RunParams &P, const SeriesDesc &d, int series, int lo, int hi, int k,
                                uint64_t g, uint32_t epoch) {
     const int lane = threadIdx.x & 31;
     int accept = 0;
@@ -304,35 +431,100 @@ __device__ void finish_segment(const RunParams &P, const SeriesDesc &d, int seri
     }
     accept = __shfl_sync(kFull, accept, 0);
     if (!accept) return;
-    const int cl_n = seg_chunks(k - lo, P.min_seg, d.kpt);
-    const int cr_n = seg_chunks(hi - k, P.min_seg, d.kpt);
-    const int tot = cl_n + cr_n;
-    if (tot == 0) return;
-    unsigned long long base = 0;
-    int ok = 0;
-    if (lane == 0) {
-        atomicAdd((unsigned long long *)&P.q->pending, (unsigned long long)tot);
-        base = atomicAdd(&P.q->tail, (unsigned long long)tot);
-        ok = base + tot <= P.q->cap;
-        if (!ok) {
-            atomicOr(&P.q->status, kStatusQueueFull);
-            atomicAdd((unsigned long long *)&P.q->pending, (unsigned long long)(-(long long)tot));
-        }
-    }
-    ok = __shfl_sync(kFull, ok, 0);
-    base = __shfl_sync(kFull, base, 0);
-    if (!ok) return;
-    for (int c = lane; c < tot; c += 32)
-        P.items[base + c] = c < cl_n ? WorkItem{series, lo, k, c} : WorkItem{series, k, hi, c - cl_n};
-    __threadfence();
-    for (int c = lane; c < tot; c += 32) st_release_u32((uint32_t *)P.ready + base + c, epoch);
+    push_segment(P, d, series, lo, k, epoch);
+    push_segment(P, d, series, k, hi, epoch);
 }
 
-// Persistent kernel: every warp independently takes tickets from the queue and scans
-// one 32-split slice per ticket.  No block-level synchronisation.
-// Scan one slice and reduce it to the warp's best (k, g); every lane gets the result.
+// 128-bit test x1 * y1 < x2 * y2 for unsigned 64-bit operands.
+__device__ __forceinline__ bool prod_less(uint64_t x1, uint64_t y1, uint64_t x2, uint64_t y2) {
+    const uint64_t h1 = __umul64hi(x1, y1), l1 = x1 * y1;
+    const uint64_t h2 = __umul64hi(x2, y2), l2 = x2 * y2;
+    return h1 < h2 || (h1 == h2 && l1 < l2);
+}
+
+// After a learned segment's probe group: (k, g) is the best exact split among its windows
+// and grid splits.  A gap (a, b) is certified when its bound cannot reach D(k):
+//   ub * den(k) < g * min(den(a + 1), den(b - 1))   (den concave, so its minimum over the
+// gap is at an end; strict, so an equal D further left cannot be missed).  All gaps
+// certified: k is the argmax.  Otherwise, if D(k) is not significant and no gap's bound
+// can be (p of the bound > alpha (1 + 1e-9), the margin covering FP64 rounding of Q),
+// the segment is not split, exactly as the full scan would decide.  Otherwise the
+// uncertified gaps are scanned by refine slices.
+__device__ __noinline__ void certify_segment(const RunParams &P, const SeriesDesc &d, const WorkItem &it, int k, uint64_t g,
+                                uint32_t epoch) {
+    const int lane = threadIdx.x & 31;
+    const int lo = it.lo, hi = it.hi;
+    CertRecord *rec = P.recs + it.rec;
+    const int n_gap = __ldcg(&rec->n_gap);
+    const uint64_t dk = (uint64_t)(k - lo) * (uint64_t)(hi - k);
+    bool open = false;  // this lane's gap is uncertified
+    int ga = 0, gb = 0;
+    uint64_t gub = 0, dmin = 1;
+    if (lane < n_gap) {
+        ga = __ldcg(&rec->a[lane]);
+        gb = __ldcg(&rec->b[lane]);
+        gub = __ldcg(&rec->ub[lane]);
+        if (gb - ga > 1) {
+            const uint64_t d1 = (uint64_t)(ga + 1 - lo) * (uint64_t)(hi - ga - 1);
+            const uint64_t d2 = (uint64_t)(gb - 1 - lo) * (uint64_t)(hi - gb + 1);
+            dmin = d1 < d2 ? d1 : d2;
+            open = !prod_less(gub, dk, g, dmin);
+        }
+    }
+    const unsigned openm = __ballot_sync(kFull, open);
+    if (openm == 0) {
+        if (lane == 0) atomicAdd(&P.q->certified, 1ull);
+        finish_segment(P, d, it.series, lo, hi, k, g, epoch);
+        return;
+    }
+    // not significant anywhere?
+    const int64_t m = d.m, H = hi - lo;
+    bool quiet = true;
+    if (lane == 0) {
+        const double pk = ks_pvalue(m * (int64_t)g, (m * (k - lo)) * (m * (hi - k)), m * H);
+        quiet = pk > P.alpha;
+    }
+    if (open) {
+        const uint64_t cap_f = (uint64_t)m * (uint64_t)H * (uint64_t)H / 4 + 1;  // |f| never exceeds m H^2 / 4
+        const uint64_t u = gub < cap_f ? gub : cap_f;
+        const double pu = ks_pvalue((int64_t)(m * (int64_t)u), (int64_t)(m * m) * (int64_t)dmin, m * H);
+        quiet = quiet && pu > P.alpha * (1.0 + 1e-9);
+    }
+    if (__all_sync(kFull, quiet)) {
+        if (lane == 0) atomicAdd(&P.q->certified, 1ull);
+        return;
+    }
+    // refine the open gaps: slices of 32 splits over a + 1 .. b - 1
+    const int ns = open ? (gb - ga - 1 + 31) / 32 : 0;
+    int incl = ns;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int tot = __shfl_sync(kFull, incl, 31);
+    unsigned long long base = 0;
+    if (lane == 0) {
+        rec->best_k = k;
+        rec->best_g = g;
+        atomicAdd(&P.q->refined, 1ull);
+        base = reserve_slots(P, tot);
+    }
+    base = __shfl_sync(kFull, base, 0);
+    if (base == ~0ull) return;
+    const int first = incl - ns;
+    for (int i = 0; i < ns; i++)
+        put_item(P, base + first + i,
+                 WorkItem{it.series, lo, hi, first + i, kRefine | (tot << 8), ga + 1 + 32 * i, gb - 1, it.rec});
+    if (lane == 0) P.gcount[base] = 0;
+    __threadfence();
+    for (int i = 0; i < ns; i++) st_release_u32((uint32_t *)P.ready + base + first + i, epoch);
+}
+
+// Scan one slice and reduce it to the warp's best (k, g) over kmin <= k <= kmax; every lane
+// gets the result.
 template <bool WIDE, int KPT>
-__device__ void slice_best(const RunParams &P, const SeriesDesc &d, int lo, int hi, int k0, int klast,
+__device__ void slice_best(const RunParams &P, const SeriesDesc &d, int lo, int hi, int k0, int kmin, int kmax,
                            StageUnion &stage, int &bk, uint64_t &bg, int &nonempty) {
     const int lane = threadIdx.x & 31;
     uint64_t g[KPT];
@@ -343,7 +535,7 @@ __device__ void slice_best(const RunParams &P, const SeriesDesc &d, int lo, int 
 #pragma unroll
     for (int q = 0; q < KPT; q++) {
         const int k = k0 + 32 * q + lane;
-        if (k <= klast && better(k, g[q], bk, bg, lo, hi)) {
+        if (k >= kmin && k <= kmax && better(k, g[q], bk, bg, lo, hi)) {
             bk = k;
             bg = g[q];
         }
@@ -351,8 +543,8 @@ __device__ void slice_best(const RunParams &P, const SeriesDesc &d, int lo, int 
     warp_best(bk, bg, lo, hi);
 }
 
-// Persistent kernel: every warp independently takes tickets from the queue and scans
-// one slice (32 * kpt splits of one segment) per ticket.  No block-level synchronisation.
+// Persistent kernel: every warp independently takes tickets from the queue and processes
+// one item per ticket.  No block-level synchronisation.
 __global__ void __launch_bounds__(kScanThreads, 4) queue_kernel(RunParams P, uint32_t epoch) {
     __shared__ StageUnion s_stage[kScanThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -362,7 +554,7 @@ __global__ void __launch_bounds__(kScanThreads, 4) queue_kernel(RunParams P, uin
 
     for (;;) {
         unsigned long long ticket = 0;
-        int4 raw = make_int4(0, 0, 0, 0);
+        int4 raw0 = make_int4(0, 0, 0, 0), raw1 = make_int4(0, 0, 0, 0);
         int state = 0;
         if (lane == 0) {
             ticket = atomicAdd(&P.q->head, 1ull);
@@ -370,7 +562,8 @@ __global__ void __launch_bounds__(kScanThreads, 4) queue_kernel(RunParams P, uin
             unsigned ns = 32;
             for (;;) {
                 if (ticket < cap && ld_acquire_u32((const uint32_t *)P.ready + ticket) >= epoch) {
-                    raw = __ldcg((const int4 *)(P.items + ticket));
+                    raw0 = __ldcg(reinterpret_cast<const int4 *>(P.items + ticket));
+                    raw1 = __ldcg(reinterpret_cast<const int4 *>(P.items + ticket) + 1);
                     state = 1;
                     break;
                 }
@@ -386,41 +579,70 @@ __global__ void __launch_bounds__(kScanThreads, 4) queue_kernel(RunParams P, uin
         state = __shfl_sync(kFull, state, 0);
         if (state == 0) break;
         ticket = __shfl_sync(kFull, ticket, 0);
-        const WorkItem it{__shfl_sync(kFull, raw.x, 0), __shfl_sync(kFull, raw.y, 0), __shfl_sync(kFull, raw.z, 0),
-                          __shfl_sync(kFull, raw.w, 0)};
+        const WorkItem it{__shfl_sync(kFull, raw0.x, 0), __shfl_sync(kFull, raw0.y, 0),
+                          __shfl_sync(kFull, raw0.z, 0), __shfl_sync(kFull, raw0.w, 0),
+                          __shfl_sync(kFull, raw1.x, 0), __shfl_sync(kFull, raw1.y, 0),
+                          __shfl_sync(kFull, raw1.z, 0), __shfl_sync(kFull, raw1.w, 0)};
         const SeriesDesc d = P.desc[it.series];
         const int lo = it.lo, hi = it.hi;
-        const int kpt = d.kpt;
-        const int k0 = lo + P.min_seg + it.chunk * 32 * kpt;
-        const int klast = min(k0 + 32 * kpt - 1, hi - P.min_seg);
+        const int kind = item_kind(it), nch = item_nch(it);
+        const int A = lo + P.min_seg, B = hi - P.min_seg;
         const uint64_t H = (uint64_t)(hi - lo);
         const bool wide = (uint64_t)d.m * H * H >= (1ull << 33);
         int nonempty = 0, bk = kNoK;
         uint64_t bg = 0;
-        if (kpt == 4) {
-            if (wide) slice_best<true, 4>(P, d, lo, hi, k0, klast, stage, bk, bg, nonempty);
-            else slice_best<false, 4>(P, d, lo, hi, k0, klast, stage, bk, bg, nonempty);
-        } else if (kpt == 2) {
-            if (wide) slice_best<true, 2>(P, d, lo, hi, k0, klast, stage, bk, bg, nonempty);
-            else slice_best<false, 2>(P, d, lo, hi, k0, klast, stage, bk, bg, nonempty);
-        } else {
-            if (wide) slice_best<true, 1>(P, d, lo, hi, k0, klast, stage, bk, bg, nonempty);
-            else slice_best<false, 1>(P, d, lo, hi, k0, klast, stage, bk, bg, nonempty);
+        if (kind == kGrid) {
+            const int ng = min(kMaxGrid, B - A + 1);
+            const int gk = lane < ng ? (ng == 1 ? A : A + (int)((int64_t)lane * (B - A) / (ng - 1))) : -1;
+            const int gn = __shfl_down_sync(kFull, gk, 1);
+            uint64_t g = 0, ub = 0;
+            scan_grid(P.lab + d.off, P.runs + d.run_base, d.nruns, d.T, lo, hi, gk, lane + 1 < ng ? gn : gk,
+                      stage.s1, g, ub, nonempty);
+            my_evals += (unsigned long long)ng * (unsigned long long)nonempty;
+            CertRecord *rec = P.recs + it.rec;
+            if (lane + 1 < ng) {
+                rec->a[lane] = gk;
+                rec->b[lane] = gn;
+                rec->ub[lane] = ub;
+            }
+            if (lane == 0) rec->n_gap = ng - 1;
+            bk = gk >= 0 ? gk : kNoK;
+            bg = gk >= 0 ? g : 0;
+            warp_best(bk, bg, lo, hi);
+        } else if (kind == kPlain) {
+            const int kpt = d.kpt;
+            const int k0 = A + it.chunk * 32 * kpt;
+            const int kmax = min(k0 + 32 * kpt - 1, B);
+            if (kpt == 4) {
+                if (wide) slice_best<true, 4>(P, d, lo, hi, k0, k0, kmax, stage, bk, bg, nonempty);
+                else slice_best<false, 4>(P, d, lo, hi, k0, k0, kmax, stage, bk, bg, nonempty);
+            } else if (kpt == 2) {
+                if (wide) slice_best<true, 2>(P, d, lo, hi, k0, k0, kmax, stage, bk, bg, nonempty);
+                else slice_best<false, 2>(P, d, lo, hi, k0, k0, kmax, stage, bk, bg, nonempty);
+            } else {
+                if (wide) slice_best<true, 1>(P, d, lo, hi, k0, k0, kmax, stage, bk, bg, nonempty);
+                else slice_best<false, 1>(P, d, lo, hi, k0, k0, kmax, stage, bk, bg, nonempty);
+            }
+            my_evals += (unsigned long long)(kmax - k0 + 1) * (unsigned long long)nonempty;
+        } else {  // window or refine slice: 32 explicit splits
+            const int k0 = it.k0;
+            const int kmin = max(k0, A), kmax = min(k0 + 31, min(it.klim, B));
+            if (wide) slice_best<true, 1>(P, d, lo, hi, k0, kmin, kmax, stage, bk, bg, nonempty);
+            else slice_best<false, 1>(P, d, lo, hi, k0, kmin, kmax, stage, bk, bg, nonempty);
+            my_evals += (unsigned long long)max(0, kmax - kmin + 1) * (unsigned long long)nonempty;
         }
-        my_evals += (unsigned long long)(klast - k0 + 1) * (unsigned long long)nonempty;
 
-        const int nch = seg_chunks(hi - lo, P.min_seg, kpt);
-        if (nch == 1) {
+        if (nch == 1 && kind == kPlain) {
             finish_segment(P, d, it.series, lo, hi, bk, bg, epoch);
         } else {
-            // write this slice's result over its consumed slot; the last slice combines
+            // write this member's result over its consumed slot; the last member combines
             const unsigned long long base = ticket - (unsigned long long)it.chunk;
             int last = 0;
             if (lane == 0) {
                 *reinterpret_cast<ChunkResult *>(P.items + ticket) = ChunkResult{bk, 0, bg};
                 __threadfence();
-                const uint32_t old = atomicAdd((uint32_t *)P.ready + base, 1u);
-                last = old == epoch + (uint32_t)nch - 1u;
+                const uint32_t old = atomicAdd(P.gcount + base, 1u);
+                last = old == (uint32_t)nch - 1u;
             }
             last = __shfl_sync(kFull, last, 0);
             if (last) {
@@ -428,7 +650,7 @@ __global__ void __launch_bounds__(kScanThreads, 4) queue_kernel(RunParams P, uin
                 int ck = kNoK;
                 uint64_t cg = 0;
                 for (int c = lane; c < nch; c += 32) {
-                    const int4 r2 = __ldcg((const int4 *)(P.items + base + c));
+                    const int4 r2 = __ldcg(reinterpret_cast<const int4 *>(P.items + base + c));
                     const uint64_t g2 = (uint64_t)(uint32_t)r2.z | ((uint64_t)(uint32_t)r2.w << 32);
                     if (better(r2.x, g2, ck, cg, lo, hi)) {
                         ck = r2.x;
@@ -436,7 +658,20 @@ __global__ void __launch_bounds__(kScanThreads, 4) queue_kernel(RunParams P, uin
                     }
                 }
                 warp_best(ck, cg, lo, hi);
-                finish_segment(P, d, it.series, lo, hi, ck, cg, epoch);
+                if (kind == kPlain) {
+                    finish_segment(P, d, it.series, lo, hi, ck, cg, epoch);
+                } else if (kind == kRefine) {
+                    const CertRecord *rec = P.recs + it.rec;
+                    const int rk = __ldcg(&rec->best_k);
+                    const uint64_t rg = __ldcg(&rec->best_g);
+                    if (better(rk, rg, ck, cg, lo, hi)) {
+                        ck = rk;
+                        cg = rg;
+                    }
+                    finish_segment(P, d, it.series, lo, hi, ck, cg, epoch);
+                } else {
+                    certify_segment(P, d, it, ck, cg, epoch);
+                }
             }
         }
         if (lane == 0) {
@@ -451,7 +686,7 @@ __global__ void __launch_bounds__(kScanThreads, 4) queue_kernel(RunParams P, uin
 // Expand the top-level slices of every series into the queue, costliest series first.
 __global__ void init_items_kernel(const SeriesDesc *__restrict__ desc, const int32_t *__restrict__ qorder,
                                   const int64_t *__restrict__ item_base, int64_t S, int32_t min_seg,
-                                  WorkItem *items, int32_t *ready, uint32_t epoch) {
+                                  WorkItem *items, int32_t *ready, uint32_t *gcount, uint32_t epoch) {
     const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (i >= S) return;
@@ -460,9 +695,26 @@ __global__ void init_items_kernel(const SeriesDesc *__restrict__ desc, const int
     const int nch = seg_chunks(T, min_seg, desc[s].kpt);
     const int64_t b = item_base[i];
     for (int c = lane; c < nch; c += 32) {
-        items[b + c] = WorkItem{s, 0, T, c};
+        int4 *dst = reinterpret_cast<int4 *>(items + b + c);
+        dst[0] = make_int4(s, 0, T, c);
+        dst[1] = make_int4(kPlain | (nch << 8), 0, T - min_seg, -1);
+        if (c == 0) gcount[b] = 0;
         ready[b + c] = (int32_t)epoch;
     }
+}
+
+// Learned segmentation: decide each series' path from its proposal confidence (plain scan
+// when conf < conf_min) and push the work for its whole range.
+__global__ void init_learned_kernel(RunParams P, const float *__restrict__ conf, float conf_min,
+                                    int32_t *__restrict__ fallback_out, int64_t S, uint32_t epoch) {
+    const int64_t s = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (s >= S) return;
+    if (lane == 0) fallback_out[s] = conf[s] < conf_min ? 1 : 0;
+    __syncwarp();
+    __threadfence_block();
+    const SeriesDesc d = P.desc[s];
+    push_segment(P, d, (int)s, 0, d.T, epoch);
 }
 
 // One warp per series: gather the flagged steps in ascending order.
@@ -519,12 +771,22 @@ cudaError_t launch_queue_run(const RunParams &P, int grid, uint32_t epoch, cudaS
     return cudaGetLastError();
 }
 
+cudaError_t launch_init_learned(const RunParams &P, const float *conf, float conf_min, int32_t *fallback_out,
+                                int64_t S, uint32_t epoch, cudaStream_t st) {
+    if (S <= 0) return cudaSuccess;
+    const int warps = 8;
+    init_learned_kernel<<<(unsigned)((S + warps - 1) / warps), warps * 32, 0, st>>>(P, conf, conf_min, fallback_out, S,
+                                                                                      epoch);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_init_items(const SeriesDesc *desc, const int32_t *qorder, const int64_t *item_base, int64_t S,
-                              int32_t min_seg, WorkItem *items, int32_t *ready, uint32_t epoch, cudaStream_t st) {
+                              int32_t min_seg, WorkItem *items, int32_t *ready, uint32_t *gcount, uint32_t epoch,
+                              cudaStream_t st) {
     if (S <= 0) return cudaSuccess;
     const int warps = 8;
     init_items_kernel<<<(unsigned)((S + warps - 1) / warps), warps * 32, 0, st>>>(desc, qorder, item_base, S, min_seg,
-                                                                                    items, ready, epoch);
+                                                                                    items, ready, gcount, epoch);
     return cudaGetLastError();
 }
 

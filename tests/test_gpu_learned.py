@@ -205,3 +205,101 @@ def test_training_reduces_loss(eng):
         eng.cnn_train_step(feat, 512, 32, cnt, idx, lr=3e-3, loss=loss)
     _, l1 = eng.cnn_grads(feat, 512, 32, cnt, idx)
     assert float(l1.item()) < 0.5 * float(l0.item())
+
+
+# ------------------------------------------------------------------ exact learned segmentation
+
+def _segment(eng, b, mode, alpha=1e-6, min_seg=1, max_cp=16):
+    r = eng.ks_segment(mt4g.to_device_samples(b.samples), b.offsets, b.steps, alpha, min_seg, max_cp, mode=mode)
+    return r.rc, [t.cpu().numpy() for t in r[1:]]
+
+
+def _assert_same(full, learned):
+    rc_f, (cf, idf, nf, df, pf, fbf) = full
+    rc_l, (cl, idl, nl, dl, pl, fbl) = learned
+    assert rc_f == rc_l
+    assert np.array_equal(cf, cl)
+    assert np.array_equal(idf, idl)
+    assert np.array_equal(nf, nl)
+    assert np.array_equal(df, dl)
+    assert np.array_equal(pf, pl)  # identical splits give identical FP64 p-values
+    assert (fbf == 0).all()
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_learned_mode_equals_full_on_config2(eng, seed):
+    import oracle
+    b = synth.generate(2, 20 + seed, 256)
+    eng.cnn_init(100 + seed)  # untrained: windows are often wrong, certification must catch it
+    eng.set_option(mt4g.OPT_CONF_MIN_PPM, 0)  # every series takes the learned path
+    try:
+        full = _segment(eng, b, mt4g.MODE_FULL)
+        learned = _segment(eng, b, mt4g.MODE_LEARNED)
+        stats = eng.learned_stats()
+    finally:
+        eng.set_option(mt4g.OPT_CONF_MIN_PPM, 900000)
+    _assert_same(full, learned)
+    assert (learned[1][5] == 0).all()  # no fallback at threshold 0
+    assert stats["probe_groups"] > 256 and stats["certified"] + stats["refined"] == stats["probe_groups"]
+    # and the oracle agrees on a sample
+    sample = np.arange(0, 256, 16)
+    sb = synth.from_arrays([b.series(s) for s in sample])
+    orc, ocnt, oidx, onum, oden, op = oracle.ks_segment(sb.samples, sb.offsets, sb.steps, 1e-6, 1, 16, nthreads=8)
+    assert np.array_equal(learned[1][0][sample], ocnt) and np.array_equal(learned[1][1][sample], oidx)
+
+
+def test_learned_mode_fallback_threshold(eng):
+    b = synth.generate(2, 31, 64)
+    eng.cnn_init(7)
+    full = _segment(eng, b, mt4g.MODE_FULL)
+    eng.set_option(mt4g.OPT_CONF_MIN_PPM, 1000001)  # nobody is confident enough
+    try:
+        rc, res = _segment(eng, b, mt4g.MODE_LEARNED)
+    finally:
+        eng.set_option(mt4g.OPT_CONF_MIN_PPM, 900000)
+    assert (res[5] == 1).all()
+    _assert_same(full, (rc, res[:5] + [np.zeros_like(res[5])]))
+
+
+def test_learned_mode_random_shapes_and_min_seg(eng):
+    rng = np.random.default_rng(17)
+    series = []
+    for _ in range(120):
+        T = int(rng.integers(2, 400))
+        m = int(rng.integers(1, 200))
+        x = rng.integers(0, int(rng.integers(2, 400)), size=(T, m))
+        for _c in range(int(rng.integers(0, 4))):
+            x[int(rng.integers(0, T)):] += int(rng.integers(0, 100))
+        series.append(x.astype(np.uint32))
+    b = synth.from_arrays(series)
+    eng.cnn_init(5)
+    eng.set_option(mt4g.OPT_CONF_MIN_PPM, 0)
+    try:
+        for alpha, min_seg in [(1e-6, 1), (1e-2, 3), (0.3, 1)]:
+            _assert_same(_segment(eng, b, mt4g.MODE_FULL, alpha, min_seg),
+                         _segment(eng, b, mt4g.MODE_LEARNED, alpha, min_seg))
+    finally:
+        eng.set_option(mt4g.OPT_CONF_MIN_PPM, 900000)
+
+
+def test_learned_mode_uneven_config3_sample(eng):
+    b3 = synth.generate(3, 2, 400)
+    keep = [s for s in range(400) if b3.m[s] <= 256 and float(b3.steps[s]) ** 2 * float(b3.m[s]) < 4e8][:120]
+    b = synth.from_arrays([b3.series(s) for s in keep])
+    eng.cnn_init(9)
+    eng.set_option(mt4g.OPT_CONF_MIN_PPM, 0)
+    try:
+        _assert_same(_segment(eng, b, mt4g.MODE_FULL), _segment(eng, b, mt4g.MODE_LEARNED))
+    finally:
+        eng.set_option(mt4g.OPT_CONF_MIN_PPM, 900000)
+
+
+def test_learned_mode_needs_weights():
+    import torch
+    e = mt4g.Engine(0)
+    b = synth.generate(1, 0, 1)
+    with pytest.raises(mt4g.Mt4gError) as err:
+        e.ks_segment(mt4g.to_device_samples(b.samples), b.offsets, b.steps, 1e-6, mode=mt4g.MODE_LEARNED)
+    assert err.value.code == mt4g.EINVAL
+    e.close()
+    torch.cuda.synchronize()

@@ -38,7 +38,7 @@ def gpu_scan(eng, b, mode=mt4g.MODE_FULL):
 
 def gpu_segment(eng, b, alpha, min_seg=1, max_cp=16, mode=mt4g.MODE_FULL):
     r = eng.ks_segment(mt4g.to_device_samples(b.samples), b.offsets, b.steps, alpha, min_seg, max_cp, mode=mode)
-    return (r.rc,) + tuple(t.cpu().numpy() for t in r[1:])
+    return (r.rc,) + tuple(t.cpu().numpy() for t in r[1:6])
 
 
 def check_scan(eng, b, mode=mt4g.MODE_FULL, nthreads=8):
