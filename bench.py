@@ -1,16 +1,23 @@
 """Benchmark of the B300 KS change-point engine.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload plain]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload learned|plain|uneven]
 
-One step = one full pass of the hot path over one batch of synthetic series that is already
-resident in HBM: per-series radix sort + run table, the all-splits exact scan, the FP64
-p-value and binary segmentation (alpha = 1e-6) through the device work queue.
-Workload "plain": 1024 series, T=512 steps, m=128 uint32 samples per step, three change points
-per series (lognormal levels 35/300/800/1100 cycles, 0.5% U{2000..10000} outliers), 268 MB of
-input per batch, larger than the 126 MB L2, so consecutive steps do not hit in L2.
+Workloads (synthetic series from the seeded generator, resident in HBM before timing):
+  learned (default): 65536 series, T=512 steps, m=128 uint32 samples per step, three change points
+      per series (lognormal levels 35/300/800/1100 cycles, 0.5% U{2000..10000} outliers), seed 4;
+      17.2 GB per batch.  One step = one learned+exact binary segmentation (alpha 1e-6): per-series
+      radix sort + run table, per-step summaries, the proposal CNN, windows, exact window and grid
+      scans with certification, refinement or full-scan fallback, FP64 p-values.  The plain full
+      exact segmentation of the same batch is timed alongside; every series' answers of the two
+      paths are compared (agreement) and the fallback rate is reported.
+  plain: 1024 series of the same distribution (seed 1), plain full exact segmentation.
+  uneven: 16384 series, T ~ U{32..4096}, m in {8,16,64,256}, 0-4 change points with level ratios
+      log-uniform in [1.01, 30], 1% Pareto(1.5) tails (seed 2); plain full segmentation, one
+      persistent-kernel launch over the whole batch.
+Every batch is larger than the 126 MB L2, so consecutive steps do not hit in L2.
 
-Prints one JSON line (rank 0).  Under torchrun each rank runs its own batch of the same shape
-(series are independent, no collective on the data path): weak scaling, value = all series
+Prints one JSON line (rank 0).  Under torchrun each rank processes its own batch of the same shape
+(series are independent; no collective on the data path): weak scaling, value = all series
 processed / the slowest rank's time.
 """
 from __future__ import annotations
@@ -30,19 +37,26 @@ sys.path.insert(0, ROOT)
 
 ALPHA = 1e-6
 MAX_CP = 16
+METRIC = "KS change-point series/s & samples/s; learned+exact vs plain at equal answers"
+WEIGHTS = os.path.join(ROOT, "paper_2511_05958_b300", "weights", "cnn_c2.bin")
 WORKLOADS = {
-    # name: (generator config, seed, series)
-    "plain": (2, 1, 1024),
+    # name: (generator config, seed, series, learned, description)
+    "learned": (2, 4, 65536, True, "learned+exact segmentation, 65536 series x T=512 x m=128 uint32 "
+                                   "(3 change points, lognormal levels, 0.5% outliers)"),
+    "plain": (2, 1, 1024, False, "plain full segmentation, 1024 series x T=512 x m=128 uint32"),
+    "uneven": (3, 2, 16384, False, "plain full segmentation, 16384 uneven series, T 32..4096, m 8..256"),
 }
+LAUNCHES = {False: 4, True: 14}  # our kernels per call (plain / learned)
+STAGES = ["upload", "sort", "proposals", "queue", "collect"]
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
-    ap.add_argument("--workload", default="plain", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="learned", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kpt", type=int, default=0, help="force the scan tile (1, 2, 4); 0 = automatic")
     ap.add_argument("--series", type=int, default=None,
@@ -51,18 +65,15 @@ def parse():
 
 
 def dist_info():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
 
 
-def workload_config(name, world):
-    cfg, seed, S = WORKLOADS[name]
-    return {"workload": "plain binary segmentation, 1024 series x T=512 x m=128 uint32 (c2 generator)",
-            "series_per_gpu": S, "T": 512, "m": 128, "alpha": ALPHA, "min_seg": 1, "max_cp": MAX_CP,
-            "global_series": S * world, "l2": "inputs (268 MB per batch) larger than L2",
-            "parallelism": f"replicas x{world} (series sharded, no collective)"}
+def workload_config(name, world, S):
+    cfg, seed, _, learned, desc = WORKLOADS[name]
+    return {"workload": desc, "series_per_gpu": S, "global_series": S * world, "alpha": ALPHA, "min_seg": 1,
+            "max_cp": MAX_CP, "generator": f"config {cfg}, seed {seed}", "learned": learned,
+            "l2": "inputs larger than L2", "parallelism": f"replicas x{world} (series sharded, no collective)"}
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -73,8 +84,7 @@ class ClockSampler:
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index):
-        self.index = index
-        self.proc = None
+        self.index, self.proc = index, None
 
     def start(self):
         try:
@@ -90,7 +100,7 @@ class ClockSampler:
         self.proc.terminate()
         out, _ = self.proc.communicate(timeout=10)
         sm, mx, reasons = [], [], set()
-        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in out.strip().splitlines():
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
@@ -100,64 +110,56 @@ class ClockSampler:
                 mx.append(float(f[2]))
             except ValueError:
                 continue
-            for n, v in zip(names[1:], f[5:9]):
+            for n, v in zip(names, f[5:9]):
                 if v.lower() == "active":
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# ----------------------------------------------------------------------------- reference arm
+# ----------------------------------------------------------------------------- oracle timing
+
+def oracle_sample(args):
+    cfg, seed, S, _, _ = WORKLOADS[args.workload]
+    import synth
+    n = {"learned": 1024, "plain": 96, "uneven": 256}[args.workload]
+    stride = max(1, S // n)
+    idx = np.arange(0, S, stride)[:n]
+    if cfg == 3:  # keep the sample's CPU time bounded: the oracle is O(T N) per segment
+        T, m, _, _ = synth.params(cfg, seed, S)
+        cost = T.astype(np.float64) ** 2 * m
+        idx = idx[cost[idx] < 2e8]
+    parts = [synth.generate(cfg, seed, 1, series_begin=int(s)).series(0) for s in idx]
+    return synth.from_arrays(parts), f"{len(idx)} of {S} series (every {stride}th" + \
+        (", cost-capped)" if cfg == 3 else ")")
+
+
+def run_oracle(sb, nthreads):
+    import oracle
+    t0 = time.perf_counter()
+    oracle.ks_segment(sb.samples, sb.offsets, sb.steps, ALPHA, 1, MAX_CP, nthreads=nthreads)
+    return time.perf_counter() - t0
+
 
 def run_reference(args, rank, world):
     """The oracle timed on the host cores, on a bounded sample of the same workload."""
     if rank != 0:
         return
-    import oracle
-    import synth
-    cfg, seed, S = WORKLOADS[args.workload]
-    sample_n = 64
-    stride = S // sample_n
-    idx = np.arange(0, S, stride)[:sample_n]
-    b = synth.generate(cfg, seed, S)
-    sb = synth.from_arrays([b.series(int(s)) for s in idx])
+    sb, desc = oracle_sample(args)
     cores = os.cpu_count() or 1
-    for _ in range(max(0, min(args.warmup, 1))):
-        oracle.ks_segment(sb.samples[:sb.offsets[1]], sb.offsets[:2], sb.steps[:1], ALPHA, 1, MAX_CP, nthreads=1)
-    times = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        oracle.ks_segment(sb.samples, sb.offsets, sb.steps, ALPHA, 1, MAX_CP, nthreads=cores)
-        times.append(time.perf_counter() - t0)
+    times = [run_oracle(sb, cores) for _ in range(args.steps)]
     t = float(np.mean(times))
-    v = len(idx) / t
-    line = {"metric": "KS change-point series/s (plain full exact segmentation)", "value": v, "unit": "series/s",
-            "impl": "reference", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "u32 samples / int64 D / f64 p", "data": "synthetic",
-            "config": workload_config(args.workload, 1),
-            "samples_per_s": v * 512 * 128,
+    v = sb.S / t
+    S = WORKLOADS[args.workload][2]
+    line = {"metric": METRIC, "value": v, "unit": "series/s", "impl": "reference", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32 samples / int64 D / f64 p", "data": "synthetic",
+            "config": workload_config(args.workload, 1, S),
+            "samples_per_s": float(v * sb.offsets[-1] / sb.S),
             "cpu_baseline": {"value": v, "unit": "series/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{len(idx)} of {S} series (every {stride}th) per step"},
+                             "sample": desc + " per step"},
             "e2e": {"value": v, "unit": "series/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
-
-
-def cpu_baseline(args):
-    import oracle
-    import synth
-    cfg, seed, S = WORKLOADS[args.workload]
-    sample_n = 96
-    stride = S // sample_n
-    idx = np.arange(0, S, stride)[:sample_n]
-    b = synth.generate(cfg, seed, S)
-    sb = synth.from_arrays([b.series(int(s)) for s in idx])
-    cores = os.cpu_count() or 1
-    t0 = time.perf_counter()
-    oracle.ks_segment(sb.samples, sb.offsets, sb.steps, ALPHA, 1, MAX_CP, nthreads=cores)
-    t = time.perf_counter() - t0
-    return {"value": len(idx) / t, "unit": "series/s", "cores": cores, "kind": "oracle",
-            "sample": f"{len(idx)} of {S} series (every {stride}th), one segmentation pass, {t:.1f} s"}
 
 
 # ----------------------------------------------------------------------------- B300 arm
@@ -169,6 +171,7 @@ def main():
         return run_reference(args, rank, world)
 
     import torch
+
     import paper_2511_05958_b300 as mt4g
     import synth
 
@@ -177,25 +180,20 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    cfg, seed, S = WORKLOADS[args.workload]
+    cfg, seed, S, learned, _ = WORKLOADS[args.workload]
     if args.series:
         S = args.series
     b = synth.generate(cfg, seed + 1000 * rank, S)
     host = torch.from_numpy(b.samples.view(np.int32)).pin_memory()
     d_samples = host.to(dev)
+    Ntot = int(b.offsets[-1])
     eng = mt4g.Engine(local)
     eng.set_option(mt4g.OPT_STAGE_TIMING, 1)
     eng.set_option(mt4g.OPT_SCAN_KPT, args.kpt)
+    if learned:
+        eng.cnn_load(WEIGHTS)
+    mode = mt4g.MODE_LEARNED if learned else mt4g.MODE_FULL
     stream = torch.cuda.current_stream(dev)
-    out = None
-
-    def step():
-        nonlocal out
-        out = eng.ks_segment(d_samples, b.offsets, b.steps, ALPHA, 1, MAX_CP, stream=stream, out=out, sync=False)
-
-    for _ in range(max(args.warmup, 3)):
-        step()
-    assert eng.wait() in (mt4g.OK, mt4g.ECAPACITY)
 
     def barrier():
         if world > 1:
@@ -203,53 +201,77 @@ def main():
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    # ---------------- device-resident timing
+    def max_over_ranks(t):
+        if world > 1:
+            import torch.distributed as dist
+            tt = torch.tensor([t], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t = float(tt.item())
+        return t
+
+    def timed(m, steps, warm, clocks=None):
+        out = None
+        for _ in range(max(warm, 3)):
+            out = eng.ks_segment(d_samples, b.offsets, b.steps, ALPHA, 1, MAX_CP, mode=m, stream=stream, out=out,
+                                 sync=False)
+        assert eng.wait() in (mt4g.OK, mt4g.ECAPACITY), eng.last_error()
+        if clocks:
+            clocks.start()
+            time.sleep(0.3)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            out = eng.ks_segment(d_samples, b.offsets, b.steps, ALPHA, 1, MAX_CP, mode=m, stream=stream, out=out,
+                                 sync=False)
+        e1.record(stream)
+        barrier()
+        clk = clocks.stop() if clocks else None
+        status = eng.wait()
+        stages = eng.stage_times(min(steps, 64))
+        return max_over_ranks(e0.elapsed_time(e1) / 1e3), out, status, stages, eng.last_work(), clk
+
     clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
-    barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-    e1.record(stream)
-    barrier()
-    clk = clocks.stop()
-    ms_total = e0.elapsed_time(e1)
-    status = eng.wait()
-    # per-stage durations of the timed calls (events the library recorded on `stream`)
-    stage_ms = eng.stage_times(min(args.steps, 64))
-    evals = eng.last_work()
-    t = ms_total / 1e3
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
-    series_total = S * world * args.steps
-    value = series_total / t
-    ms_step = t / args.steps * 1e3
+    t_main, out_main, status, stages, evals, clk = timed(mode, args.steps, args.warmup, clocks)
+    stats = eng.learned_stats() if learned else None
+    value = S * world * args.steps / t_main
+    line = {"metric": METRIC, "value": value, "unit": "series/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_main / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32 samples / int32-int64 exact D / f64 p"
+            + (" / bf16-fp32 proposal CNN" if learned else ""), "data": "synthetic",
+            "config": workload_config(args.workload, world, S), "samples_per_s": value * Ntot / S,
+            "status": int(status), "gpu_launches": LAUNCHES[learned] * args.steps}
+    if learned:
+        res_l = [x.clone() for x in out_main[1:6]]
+        fb = out_main[6].clone()
+        t_plain, out_plain, _, stages_p, evals_p, _ = timed(mt4g.MODE_FULL, args.steps, 1)
+        same = torch.ones(S, dtype=torch.bool, device=dev)
+        for a, c in zip(res_l, out_plain[1:6]):
+            same &= (a == c).reshape(S, -1).all(dim=1)
+        plain_value = S * world * args.steps / t_plain
+        line.update({"plain_value": plain_value, "plain_ms_per_step": t_plain / args.steps * 1e3,
+                     "speedup_vs_plain": value / plain_value, "agreement": float(same.float().mean().item()),
+                     "fallback_rate": float(fb.float().mean().item()),
+                     "certified_segments": stats["certified"], "refined_segments": stats["refined"],
+                     "evals_learned": evals, "evals_plain": evals_p,
+                     "plain_stage_ms": dict(zip(STAGES, np.asarray(stages_p).mean(axis=0).tolist()))})
 
     # ---------------- end to end through host buffers (pinned), copies in the timed region
-    res_host = None
-    d2h_bytes = S * 4 + S * MAX_CP * (4 + 8 + 8 + 8)
-    h2d_bytes = b.samples.nbytes + b.offsets.nbytes + b.steps.nbytes
+    d2h = S * 4 + S * MAX_CP * (4 + 8 + 8 + 8) + (S * 4 if learned else 0)
+    h2d = b.samples.nbytes + b.offsets.nbytes + b.steps.nbytes
+    e_steps = max(1, min(args.steps, 5))
     barrier()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(e_steps):
         d_in = host.to(dev, non_blocking=True)
-        r = eng.ks_segment(d_in, b.offsets, b.steps, ALPHA, 1, MAX_CP, stream=stream, sync=False)
-        res_host = [x.to("cpu", non_blocking=True) for x in r[1:]]
+        r = eng.ks_segment(d_in, b.offsets, b.steps, ALPHA, 1, MAX_CP, mode=mode, stream=stream, sync=False)
+        _ = [x.to("cpu", non_blocking=True) for x in r[1:]]
     f1.record(stream)
     barrier()
-    te = f0.elapsed_time(f1) / 1e3
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([te], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        te = float(tt.item())
-    e2e_value = series_total / te
+    te = max_over_ranks(f0.elapsed_time(f1) / 1e3)
+    line["e2e"] = {"value": S * world * e_steps / te, "unit": "series/s", "h2d_bytes_per_step": int(h2d),
+                   "d2h_bytes_per_step": int(d2h), "steps": e_steps}
 
     # ---------------- roofline of the dominant kernel
     peaks = {}
@@ -259,43 +281,39 @@ def main():
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6400.0))
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    st = np.asarray(stage_ms)  # [steps, stages] ms: upload, sort, queue, collect
-    sort_ms = float(st[:, 1].mean())
-    queue_ms = float(st[:, 2].mean())
-    Ntot = int(b.offsets[-1])
+    ms = dict(zip(STAGES, np.asarray(stages).mean(axis=0).tolist()))
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    sm_mhz = clk.get("sm_mhz") or 2032.0
-    evals = float(evals)
-    if queue_ms >= sort_ms:
-        # INT32 ALU bound: 4 integer ops (2 multiply-adds, |.|, max) per (split k, distinct value)
+    sm_mhz = (clk or {}).get("sm_mhz") or 2032.0
+    if ms["queue"] >= ms["sort"] and ms["queue"] >= ms["proposals"]:
         ops = 4.0 * evals
-        achieved = ops / (queue_ms / 1e3) / 1e12
+        achieved = ops / (ms["queue"] / 1e3) / 1e12
         peak = sms * 128 * sm_mhz * 1e6 / 1e12
-        roof = {"kernel": "queue_kernel (all-splits scan + p-value + segmentation)", "bound": "alu",
-                "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-                "traffic": None, "algorithmic_units": f"{evals:.4g} (k, distinct value) evaluations x 4 int ops",
-                "peak_source": f"{sms} SMs x 128 INT32 lanes x {sm_mhz:.0f} MHz median SM clock"}
-    else:
+        roof = {"kernel": "queue_kernel (exact scans, p-values, segmentation)", "bound": "alu",
+                "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak, "traffic": None,
+                "algorithmic_units": f"{evals:.4g} (split, distinct value) evaluations x 4 int ops",
+                "peak_source": f"{sms} SMs x 128 INT32 lanes x {sm_mhz:.0f} MHz (median SM clock under load)"}
+    elif ms["sort"] >= ms["proposals"]:
         byts = 10.0 * Ntot
-        achieved = byts / (sort_ms / 1e3) / 1e9
+        achieved = byts / (ms["sort"] / 1e3) / 1e9
         roof = {"kernel": "sort_series_kernel (radix sort + run table)", "bound": "hbm", "achieved": achieved,
                 "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
                 "algorithmic_units": f"{Ntot} samples x 10 B (4 B read + 6 B sorted value/label written)",
-                "peak_source": f"{hbm_src} HBM copy bandwidth"}
-    roof["stage_ms"] = {"upload": float(st[:, 0].mean()), "sort": sort_ms, "queue": queue_ms,
-                        "collect": float(st[:, 3].mean())}
-
-    line = {"metric": "KS change-point series/s (plain full exact segmentation)", "value": value,
-            "unit": "series/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "u32 samples / int32-int64 exact D / f64 p", "data": "synthetic",
-            "config": workload_config(args.workload, world), "samples_per_s": value * 512 * 128,
-            "status": int(status), "gpu_launches": 3 * args.steps,
-            "e2e": {"value": e2e_value, "unit": "series/s", "h2d_bytes_per_step": int(h2d_bytes),
-                    "d2h_bytes_per_step": int(d2h_bytes)},
-            "roofline": roof, "clocks": clk}
+                "peak_source": f"{hbm_src} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+    else:
+        byts = 4.0 * Ntot
+        achieved = byts / (ms["proposals"] / 1e3) / 1e9
+        roof = {"kernel": "summaries + CNN + windows", "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                "algorithmic_units": f"{Ntot} samples x 4 B read", "peak_source": f"{hbm_src} HBM copy bandwidth"}
+    roof["stage_ms"] = ms
+    line["roofline"] = roof
+    line["clocks"] = clk
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args)
+        sb, desc = oracle_sample(args)
+        cores = os.cpu_count() or 1
+        t = run_oracle(sb, cores)
+        line["cpu_baseline"] = {"value": sb.S / t, "unit": "series/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{desc}, one segmentation pass, {t:.1f} s"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     eng.close()

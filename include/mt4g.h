@@ -204,8 +204,8 @@ int mt4g_propose(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets,
  *
  * mt4g_stage_times: with MT4G_OPT_STAGE_TIMING on, each call records CUDA events on its
  * stream between its stages; this writes, for the last n calls (at most 64, oldest
- * first), 4 durations in ms per call: [table upload, reduce+sort+run table, work-queue
- * kernel, collect].  Synchronises on those events.  Returns the number of calls written
+ * first), 5 durations in ms per call: [table upload, reduce + sort + run table,
+ * features + network + windows (learned mode, else 0), work-queue kernel, collect].  Synchronises on those events.  Returns the number of calls written
  * (>= 0) or a negative error code.
  *
  * mt4g_last_work: after mt4g_wait(), the number of (split k, distinct value) pairs the

@@ -169,8 +169,8 @@ class Engine:
         self._check(self._L.mt4g_set_option(self._h, option, int(value)))
 
     def stage_times(self, max_calls: int = 1) -> np.ndarray:
-        """[n, 4] ms per call (upload, sort, queue kernel, collect) for the last n <= 64 calls."""
-        buf = np.zeros((max_calls, 4), np.float64)
+        """[n, 5] ms per call (upload, sort, proposals, queue kernel, collect), last n <= 64 calls."""
+        buf = np.zeros((max_calls, 5), np.float64)
         n = self._L.mt4g_stage_times(self._h, buf.ctypes.data_as(ctypes.c_void_p), max_calls)
         if n < 0:
             self._check(n)

@@ -45,7 +45,7 @@ struct mt4g_ctx {
 
     // stage timing: events of the last kTimingRing calls
     static constexpr int kTimingRing = 64;
-    static constexpr int kMarks = 5;
+    static constexpr int kMarks = 6;
     bool timing = false;
     bool events_made = false;
     cudaEvent_t ev[kTimingRing][kMarks] = {};
@@ -395,7 +395,7 @@ int enqueue_pipeline(mt4g_ctx *ctx, const uint32_t *samples, Plan &P, RunParams 
 int enqueue_proposals(mt4g_ctx *ctx, const uint32_t *samples, Plan &P, Buffers &B, RunParams &R, cudaStream_t st);
 
 int finish_call(mt4g_ctx *ctx, Buffers &B, cudaStream_t st) {
-    mark(ctx, 4, st);
+    mark(ctx, 5, st);
     if (ctx->timing) {
         ctx->ring_pos = (ctx->ring_pos + 1) % mt4g_ctx::kTimingRing;
         ctx->ring_count = std::min(ctx->ring_count + 1, mt4g_ctx::kTimingRing);
@@ -541,8 +541,9 @@ int mt4g_ks_scan(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets,
     R.dnum_out = dnum_out;
     R.dden_out = dden_out;
     R.p_out = p_out;
-    CUDA_TRY(ctx, launch_queue_run(R, ctx->grid, (uint32_t)epoch, st));
     mark(ctx, 3, st);
+    CUDA_TRY(ctx, launch_queue_run(R, ctx->grid, (uint32_t)epoch, st));
+    mark(ctx, 4, st);
     return finish_call(ctx, B, st);
 }
 
@@ -577,12 +578,14 @@ int mt4g_ks_segment(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offse
     if (P.learned) {
         rc = enqueue_proposals(ctx, samples, P, B, R, st);
         if (rc) return rc;
+        mark(ctx, 3, st);
         CUDA_TRY(ctx, launch_init_learned(R, ctx->learned_conf, ctx->conf_min, B.fallback, P.S, (uint32_t)epoch, st));
     } else {
         CUDA_TRY(ctx, cudaMemsetAsync(B.fallback, 0, P.S * sizeof(int32_t), st));
     }
+    if (!P.learned) mark(ctx, 3, st);
     CUDA_TRY(ctx, launch_queue_run(R, ctx->grid, (uint32_t)epoch, st));
-    mark(ctx, 3, st);
+    mark(ctx, 4, st);
     CUDA_TRY(ctx, launch_collect(B.desc, P.S, B.cp_flag, B.cp_num, B.cp_den, B.cp_p, max_cp, cp_count, cp_idx, dnum,
                                  dden, p, B.q, st));
     if (fallback)
@@ -883,6 +886,7 @@ int mt4g_summaries(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offset
     if (epoch < 0) return epoch;
     CUDA_TRY(ctx, launch_summaries(samples, B.desc, S, feat_out, st));
     mark(ctx, 3, st);
+    mark(ctx, 4, st);
     return finish_call(ctx, B, st);
 }
 
@@ -1000,6 +1004,7 @@ int mt4g_propose(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets,
     CUDA_TRY(ctx, cnn_forward(ctx->cnn, C.feat, C.A, B.desc, C.tiles_before, S, ntiles, st));
     CUDA_TRY(ctx, launch_propose(C.A.logits, B.desc, S, n_win, half_width, win_center, conf, st));
     mark(ctx, 3, st);
+    mark(ctx, 4, st);
     return finish_call(ctx, B, st);
 }
 

@@ -264,15 +264,19 @@ __device__ void scan_slice(const uint16_t *__restrict__ lab, const int32_t *__re
 // ---------------------------------------------------------------- grid columns and gap bounds
 
 // Exact columns at this lane's grid split gk (gk < 0: inactive lane) and, with the next
-// lane's split gn, a bound over the gap: for every split k in [gk, gn] and every x,
-//   H c_L^gk(x) - (gn - lo) C(x)  <=  H c_L^k(x) - (k - lo) C(x)  <=  H c_L^gn(x) - (gk - lo) C(x),
-// because c_L^k grows with k.  So |H c_L^k - (k - lo) C| is at most the larger modulus of
-// the two ends, and its maximum over x bounds g_k for the whole gap.
-__device__ __noinline__ void scan_grid(const uint16_t *__restrict__ lab, const int32_t *__restrict__ rt, int U, int T, int lo,
-                          int hi, int gk, int gn, SliceStage<1> &st, uint64_t &g_out, uint64_t &ub_out,
-                          int &nonempty) {
+// lane's split gn, a bound over the gap.  With f_k(x) = H c_L^k(x) - (k - lo) C(x),
+// D = Delta(x) = c_L^gn - c_L^gk, N = m H, and the fact that a step holds m samples
+// (0 <= c_L^k - c_L^gk <= m (k - gk), 0 <= c_L^gn - c_L^k <= m (gn - k)), every split k in
+// [gk, gn] satisfies, for every x,
+//   m f_k in [m f_gk - ((gn - gk) m - D) C,  m f_gk + D (N - C)]     (from the left end)
+//   m f_k in [m f_gn - D (N - C),  m f_gn + ((gn - gk) m - D) C]     (from the right end)
+// (the extremes of H (c_L^k - c_L^gk) - (k - gk) C over the admissible c_L^k).  The larger
+// modulus of the intersected interval, maximised over x, bounds m g_k over the gap.
+__device__ __noinline__ void scan_grid(const uint16_t *__restrict__ lab, const int32_t *__restrict__ rt, int U,
+                                       int T, int lo, int hi, int m, int gk, int gn, SliceStage<1> &st,
+                                       uint64_t &g_out, uint64_t &ubm_out, int &nonempty) {
     const int lane = threadIdx.x & 31;
-    const int64_t H = hi - lo;
+    const int64_t H = hi - lo, M = m, N = M * H, w = (int64_t)(gn - gk) * M;
     const int64_t a = gk - lo, an = gn - lo;
     int64_t cl = 0, C = 0;
     uint64_t mx = 0, ub = 0;
@@ -308,15 +312,18 @@ __device__ __noinline__ void scan_grid(const uint16_t *__restrict__ lab, const i
             const int64_t f = H * cl - a * C;
             const uint64_t af = (uint64_t)(f < 0 ? -f : f);
             mx = af > mx ? af : mx;
-            const int64_t u1 = H * cn - a * C, u2 = H * cl - an * C;
-            const uint64_t au = max((uint64_t)(u1 < 0 ? -u1 : u1), (uint64_t)(u2 < 0 ? -u2 : u2));
+            const int64_t fn = H * cn - an * C;
+            const int64_t dl = cn - cl;
+            const int64_t up = min(M * f + dl * (N - C), M * fn + (w - dl) * C);
+            const int64_t dn = max(M * f - (w - dl) * C, M * fn - dl * (N - C));
+            const uint64_t au = max((uint64_t)(up < 0 ? -up : up), (uint64_t)(dn < 0 ? -dn : dn));
             ub = au > ub ? au : ub;
         }
         nonempty += cnt;
         __syncwarp();
     }
     g_out = mx;
-    ub_out = ub;
+    ubm_out = ub;
 }
 
 // ---------------------------------------------------------------- queue helpers
@@ -354,14 +361,35 @@ __device__ __forceinline__ void put_item(const RunParams &P, unsigned long long 
 }
 
 // Push the work for segment [lo, hi) (all lanes of a warp call it with the same arguments).
-// Plain series: the slices of the full scan.  Learned series: a probe group of the window
-// slices that reach the segment's splits plus one grid item.
+// Plain series, and learned segments with no window centred at least half/2 inside their
+// splits: the slices of the full scan.  Other learned segments: a probe group of the
+// window slices that reach the segment's splits plus one grid item.
 __device__ __noinline__ void push_segment(const RunParams &P, const SeriesDesc &d, int series, int lo, int hi, uint32_t epoch) {
     const int lane = threadIdx.x & 31;
     const int A = lo + P.min_seg, B = hi - P.min_seg;
     if (B < A) return;
     const bool learned = P.mode == kRunLearned && !P.fallback[series];
     if (!learned) {
+        const int nch = seg_chunks(hi - lo, P.min_seg, d.kpt);
+        unsigned long long base = 0;
+        if (lane == 0) base = reserve_slots(P, nch);
+        base = __shfl_sync(kFull, base, 0);
+        if (base == ~0ull) return;
+        for (int c = lane; c < nch; c += 32)
+            put_item(P, base + c, WorkItem{series, lo, hi, c, kPlain | (nch << 8), 0, B, -1});
+        if (lane == 0) P.gcount[base] = 0;
+        __threadfence();
+        for (int c = lane; c < nch; c += 32) st_release_u32((uint32_t *)P.ready + base + c, epoch);
+        return;
+    }
+    // a probe only pays where a window is centred well inside the segment; elsewhere (in
+    // particular the pieces between consecutive change points) the full scan decides
+    int inner = 0;
+    if (lane < P.n_win) {
+        const int c = P.win_center[(int64_t)series * P.n_win + lane];
+        inner = c >= A + P.half / 2 && c <= B - P.half / 2;
+    }
+    if (__ballot_sync(kFull, inner) == 0) {
         const int nch = seg_chunks(hi - lo, P.min_seg, d.kpt);
         unsigned long long base = 0;
         if (lane == 0) base = reserve_slots(P, nch);
@@ -595,9 +623,10 @@ __global__ void __launch_bounds__(kScanThreads, 4) queue_kernel(RunParams P, uin
             const int ng = min(kMaxGrid, B - A + 1);
             const int gk = lane < ng ? (ng == 1 ? A : A + (int)((int64_t)lane * (B - A) / (ng - 1))) : -1;
             const int gn = __shfl_down_sync(kFull, gk, 1);
-            uint64_t g = 0, ub = 0;
-            scan_grid(P.lab + d.off, P.runs + d.run_base, d.nruns, d.T, lo, hi, gk, lane + 1 < ng ? gn : gk,
-                      stage.s1, g, ub, nonempty);
+            uint64_t g = 0, ubm = 0;
+            scan_grid(P.lab + d.off, P.runs + d.run_base, d.nruns, d.T, lo, hi, d.m, gk, lane + 1 < ng ? gn : gk,
+                      stage.s1, g, ubm, nonempty);
+            const uint64_t ub = (ubm + (uint64_t)d.m - 1) / (uint64_t)d.m;  // bound on g over the gap
             my_evals += (unsigned long long)ng * (unsigned long long)nonempty;
             CertRecord *rec = P.recs + it.rec;
             if (lane + 1 < ng) {

@@ -128,3 +128,54 @@ def from_arrays(series_list) -> Batch:
         if series_list else np.zeros(0, np.uint32)
     S = len(series_list)
     return Batch(samples, offsets, T, m, np.zeros(S, np.int32), -np.ones((S, MAX_CP), np.int32))
+
+
+# ----------------------------------------------------------------------------- GPU twin
+
+_SRC_GPU = os.path.join(_HERE, "gen_gpu.cu")
+_LIB_GPU = os.path.join(_HERE, "libmt4g_synth_gpu.so")
+_lib_gpu = None
+
+
+def build_gpu(force: bool = False) -> str:
+    """Compile gen_gpu.cu (the FP32 GPU twin of the generator) for sm_103a."""
+    if force or not os.path.exists(_LIB_GPU) or os.path.getmtime(_LIB_GPU) < os.path.getmtime(_SRC_GPU):
+        tmp = _LIB_GPU + f".tmp{os.getpid()}"
+        subprocess.check_call(["/usr/local/cuda/bin/nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3",
+                               "-Xcompiler", "-fPIC", "-shared", "-cudart", "shared", "-o", tmp, _SRC_GPU,
+                               "-Xlinker", "-rpath,/usr/local/cuda/lib64"])
+        os.replace(tmp, _LIB_GPU)
+    return _LIB_GPU
+
+
+def _load_gpu():
+    global _lib_gpu
+    if _lib_gpu is None:
+        build_gpu()
+        lib = ctypes.CDLL(_LIB_GPU)
+        lib.mt4g_synth_fill_gpu.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64,
+                                            ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        lib.mt4g_synth_fill_gpu.restype = ctypes.c_int
+        _lib_gpu = lib
+    return _lib_gpu
+
+
+def generate_gpu(cfg: int, seed: int, count: int, series_begin: int = 0, device="cuda", stream=None):
+    """Generate series on the GPU (same recipe and seeds as generate(), FP32 draws, so values differ).
+
+    Returns (samples as a device int32 tensor holding the uint32 bits, Batch with host shapes and
+    truth; its .samples is None).
+    """
+    import torch
+    T, m, ncp, cps = params(cfg, seed, count, series_begin)
+    offsets = np.zeros(count + 1, np.int64)
+    np.cumsum(T.astype(np.int64) * m.astype(np.int64), out=offsets[1:])
+    d_off = torch.from_numpy(offsets).to(device)
+    samples = torch.empty(int(offsets[-1]), dtype=torch.int32, device=device)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    rc = _load_gpu().mt4g_synth_fill_gpu(cfg, seed, series_begin, count, int(T.max()),
+                                         ctypes.c_void_p(d_off.data_ptr()), ctypes.c_void_p(samples.data_ptr()),
+                                         ctypes.c_void_p(st.cuda_stream))
+    if rc != 0:
+        raise RuntimeError(f"mt4g_synth_fill_gpu failed ({rc})")
+    return samples, Batch(None, offsets, T, m, ncp, cps)
