@@ -200,6 +200,32 @@ int mt4g_propose(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets,
                  int32_t n_win, int32_t half_width, int32_t *win_center, float *conf, void *cuda_stream);
 
 /*
+ * Allocation-free variant of mt4g_ks_scan (no counterpart in the paper).
+ *
+ * For callers that cannot allocate device (or host) memory: code running inside a memory
+ * pool or arena it does not own, callers in the middle of a stream capture, or processes
+ * that forbid allocation after start-up.  Same arguments and results as mt4g_ks_scan in
+ * MT4G_MODE_FULL (top-level test over every split of every series), but without a context:
+ * all scratch comes from one static device array of MT4G_NOALLOC_SCRATCH_BYTES that every
+ * GPU loading this library holds until the process exits, and host tables from a static
+ * host buffer.  Limits: S <= MT4G_NOALLOC_MAX_SERIES, total samples <=
+ * MT4G_NOALLOC_MAX_SAMPLES, total steps <= MT4G_NOALLOC_MAX_STEPS; beyond them the call
+ * returns MT4G_EINVAL before touching the GPU.  It runs on the current CUDA device.
+ * The array keeps the last call's contents and is shared by all calls on a device: the
+ * call clears what must start at zero, but calls whose GPU work overlaps (different
+ * streams or host threads) race on it.  The first call on a device looks up the array's
+ * address (cudaGetSymbolAddress), so make that first call before any stream capture.  The
+ * call is synchronous: it returns after the outputs are written, with MT4G_OK,
+ * MT4G_EINVAL, MT4G_ECUDA, MT4G_ETIMEOUT or MT4G_ECAPACITY.
+ */
+#define MT4G_NOALLOC_SCRATCH_BYTES (12u << 20)
+#define MT4G_NOALLOC_MAX_SERIES 4096
+#define MT4G_NOALLOC_MAX_SAMPLES (1 << 19)
+#define MT4G_NOALLOC_MAX_STEPS (1 << 16)
+int mt4g_ks_scan_noalloc(const uint32_t *samples, const int64_t *offsets, const int32_t *steps, int64_t S,
+                         int32_t *k_out, int64_t *dnum_out, int64_t *dden_out, double *p_out, void *cuda_stream);
+
+/*
  * Measurement helpers (no counterpart in the paper; they instrument the calls above).
  *
  * mt4g_stage_times: with MT4G_OPT_STAGE_TIMING on, each call records CUDA events on its

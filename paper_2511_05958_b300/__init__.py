@@ -62,6 +62,7 @@ def load_library():
     L.mt4g_ks_scan.argtypes = [vp, vp, vp, vp, i64, i32, vp, vp, vp, vp, vp]
     L.mt4g_ks_segment.argtypes = [vp, vp, vp, vp, i64, dbl, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp]
     L.mt4g_learned_stats.argtypes = [vp, vp]
+    L.mt4g_ks_scan_noalloc.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp, vp]
     L.mt4g_stage_times.argtypes = [vp, vp, i32]
     L.mt4g_last_work.argtypes = [vp, vp]
     L.mt4g_summaries.argtypes = [vp, vp, vp, vp, i64, vp, vp]
@@ -84,7 +85,7 @@ def exported_symbols():
             "mt4g_ks_scan", "mt4g_ks_segment", "mt4g_stage_times", "mt4g_last_work",
             "mt4g_summaries", "mt4g_cnn_init", "mt4g_cnn_get_params", "mt4g_cnn_set_params", "mt4g_cnn_save",
             "mt4g_cnn_load", "mt4g_cnn_forward", "mt4g_cnn_grads", "mt4g_cnn_train_step", "mt4g_propose",
-            "mt4g_learned_stats"]
+            "mt4g_learned_stats", "mt4g_ks_scan_noalloc"]
 
 
 class ScanResult(NamedTuple):
@@ -322,6 +323,26 @@ def _mixin_learned(cls):
 
 
 Engine = _mixin_learned(Engine)
+
+
+NOALLOC_MAX_SERIES, NOALLOC_MAX_SAMPLES, NOALLOC_MAX_STEPS = 4096, 1 << 19, 1 << 16
+
+
+def ks_scan_noalloc(samples, offsets, steps, out, stream=None) -> int:
+    """mt4g_ks_scan_noalloc: the top-level scan without any allocation by the library.
+
+    For callers that cannot allocate (memory owned by another pool, an ongoing stream
+    capture, allocation forbidden after start-up).  ``out`` must be a ScanResult of
+    preallocated device tensors; returns the C status code.  Runs on the current device and
+    synchronises ``stream``.  Limits: NOALLOC_MAX_SERIES series, NOALLOC_MAX_SAMPLES samples,
+    NOALLOC_MAX_STEPS steps in total.
+    """
+    L = load_library()
+    offsets, steps = _host_tables(offsets, steps)
+    return int(L.mt4g_ks_scan_noalloc(_dev_ptr(samples, "samples"), offsets.ctypes.data_as(ctypes.c_void_p),
+                                      steps.ctypes.data_as(ctypes.c_void_p), steps.shape[0], _dev_ptr(out.k, "k"),
+                                      _dev_ptr(out.dnum, "dnum"), _dev_ptr(out.dden, "dden"), _dev_ptr(out.p, "p"),
+                                      _stream_handle(stream)))
 
 
 def to_device_samples(samples: np.ndarray, device="cuda"):
