@@ -29,7 +29,7 @@ namespace mt4g {
 
 namespace {
 
-constexpr int kTile = 64;  // positions per block
+constexpr int kTile = 128;  // positions per block
 
 __device__ __forceinline__ float bf(const __nv_bfloat16 v) { return __bfloat162float(v); }
 
@@ -51,20 +51,21 @@ __device__ __forceinline__ int64_t find_series(const int64_t *__restrict__ tiles
 // is an FP32 gradient, W is the flipped transpose, and the result is multiplied by the
 // mask (act > 0) and stored FP32 without bias.
 template <int CIN, typename TIn, bool BWD>
-__global__ void __launch_bounds__(256) conv32_kernel(const TIn *__restrict__ in, const float *__restrict__ W,
+__global__ void __launch_bounds__(128) conv32_kernel(const TIn *__restrict__ in, const float *__restrict__ W,
                                                      const float *__restrict__ bias, void *__restrict__ out,
                                                      const __nv_bfloat16 *__restrict__ mask_act,
                                                      const SeriesDesc *__restrict__ desc,
                                                      const int64_t *__restrict__ tiles_before, int64_t S) {
+    constexpr int kP = 4;  // positions per thread (consecutive)
     __shared__ float xs[kTile + 4][CIN + 1];
     __shared__ __align__(16) float ws[5 * CIN][32];
     const int64_t tile = blockIdx.x;
     const int64_t s = find_series(tiles_before, S, tile);
     const SeriesDesc d = desc[s];
     const int t0 = (int)(tile - tiles_before[s]) * kTile;
-    const int64_t r0 = row_base(d, s) + t0;  // padded row of window start for position t0
+    const int64_t r0 = row_base(d, s) + t0;  // padded row of the window start of position t0
     const int nrows = min(kTile + 4, d.T + 4 - t0);
-    for (int e = threadIdx.x; e < (kTile + 4) * CIN; e += 256) {
+    for (int e = threadIdx.x; e < (kTile + 4) * CIN; e += 128) {
         const int r = e / CIN, c = e % CIN;
         float v = 0.f;
         if (r < nrows) {
@@ -75,40 +76,49 @@ __global__ void __launch_bounds__(256) conv32_kernel(const TIn *__restrict__ in,
         }
         xs[r][c] = v;
     }
-    for (int e = threadIdx.x; e < 5 * CIN * 32; e += 256) ws[e / 32][e % 32] = W[e];
+    for (int e = threadIdx.x; e < 5 * CIN * 32; e += 128) ws[e / 32][e % 32] = W[e];
     __syncthreads();
-    const int p = threadIdx.x >> 2, og = threadIdx.x & 3;
-    float acc[8];
+    const int p0 = (threadIdx.x >> 2) * kP, og = threadIdx.x & 3;
+    float acc[kP][8];
 #pragma unroll
-    for (int j = 0; j < 8; j++) acc[j] = BWD ? 0.f : bias[og * 8 + j];
+    for (int q = 0; q < kP; q++)
+#pragma unroll
+        for (int j = 0; j < 8; j++) acc[q][j] = BWD ? 0.f : bias[og * 8 + j];
 #pragma unroll
     for (int dd = 0; dd < 5; dd++) {
-#pragma unroll 4
+#pragma unroll 2
         for (int i = 0; i < CIN; i++) {
-            const float x = xs[p + dd][i];
             const float4 w0 = *reinterpret_cast<const float4 *>(&ws[dd * CIN + i][og * 8]);
             const float4 w1 = *reinterpret_cast<const float4 *>(&ws[dd * CIN + i][og * 8 + 4]);
-            acc[0] = fmaf(x, w0.x, acc[0]);
-            acc[1] = fmaf(x, w0.y, acc[1]);
-            acc[2] = fmaf(x, w0.z, acc[2]);
-            acc[3] = fmaf(x, w0.w, acc[3]);
-            acc[4] = fmaf(x, w1.x, acc[4]);
-            acc[5] = fmaf(x, w1.y, acc[5]);
-            acc[6] = fmaf(x, w1.z, acc[6]);
-            acc[7] = fmaf(x, w1.w, acc[7]);
+#pragma unroll
+            for (int q = 0; q < kP; q++) {
+                const float x = xs[p0 + q + dd][i];
+                acc[q][0] = fmaf(x, w0.x, acc[q][0]);
+                acc[q][1] = fmaf(x, w0.y, acc[q][1]);
+                acc[q][2] = fmaf(x, w0.z, acc[q][2]);
+                acc[q][3] = fmaf(x, w0.w, acc[q][3]);
+                acc[q][4] = fmaf(x, w1.x, acc[q][4]);
+                acc[q][5] = fmaf(x, w1.y, acc[q][5]);
+                acc[q][6] = fmaf(x, w1.z, acc[q][6]);
+                acc[q][7] = fmaf(x, w1.w, acc[q][7]);
+            }
         }
     }
-    if (t0 + p >= d.T) return;
-    const int64_t row = r0 + 2 + p;
-    if (!BWD) {
-        __nv_bfloat16 *o = reinterpret_cast<__nv_bfloat16 *>(out) + row * 32 + og * 8;
 #pragma unroll
-        for (int j = 0; j < 8; j++) o[j] = __float2bfloat16_rn(fmaxf(acc[j], 0.f));
-    } else {
-        float *o = reinterpret_cast<float *>(out) + row * 32 + og * 8;
-        const __nv_bfloat16 *ma = mask_act + row * 32 + og * 8;
+    for (int q = 0; q < kP; q++) {
+        if (t0 + p0 + q >= d.T) break;
+        const int64_t row = r0 + 2 + p0 + q;
+        if (!BWD) {
+            __nv_bfloat162 *o = reinterpret_cast<__nv_bfloat162 *>(reinterpret_cast<__nv_bfloat16 *>(out) + row * 32 + og * 8);
 #pragma unroll
-        for (int j = 0; j < 8; j++) o[j] = bf(ma[j]) > 0.f ? acc[j] : 0.f;
+            for (int j = 0; j < 4; j++)
+                o[j] = __floats2bfloat162_rn(fmaxf(acc[q][2 * j], 0.f), fmaxf(acc[q][2 * j + 1], 0.f));
+        } else {
+            float *o = reinterpret_cast<float *>(out) + row * 32 + og * 8;
+            const __nv_bfloat16 *ma = mask_act + row * 32 + og * 8;
+#pragma unroll
+            for (int j = 0; j < 8; j++) o[j] = bf(ma[j]) > 0.f ? acc[q][j] : 0.f;
+        }
     }
 }
 
@@ -344,12 +354,12 @@ cudaError_t cnn_forward(const CnnState &W, const uint16_t *feat, const CnnActs &
     if (ntiles <= 0) return cudaSuccess;
     const __nv_bfloat16 *x0 = reinterpret_cast<const __nv_bfloat16 *>(feat);
     const float *u = W.used;
-    conv32_kernel<kFeatC, __nv_bfloat16, false><<<(unsigned)ntiles, 256, 0, st>>>(
+    conv32_kernel<kFeatC, __nv_bfloat16, false><<<(unsigned)ntiles, 128, 0, st>>>(
         x0, u + cnn_off(0), u + cnn_off(1), A.a1, nullptr, desc, tiles_before, S);
-    conv32_kernel<32, __nv_bfloat16, false><<<(unsigned)ntiles, 256, 0, st>>>(
+    conv32_kernel<32, __nv_bfloat16, false><<<(unsigned)ntiles, 128, 0, st>>>(
         reinterpret_cast<const __nv_bfloat16 *>(A.a1), u + cnn_off(2), u + cnn_off(3), A.a2, nullptr, desc,
         tiles_before, S);
-    conv32_kernel<32, __nv_bfloat16, false><<<(unsigned)ntiles, 256, 0, st>>>(
+    conv32_kernel<32, __nv_bfloat16, false><<<(unsigned)ntiles, 128, 0, st>>>(
         reinterpret_cast<const __nv_bfloat16 *>(A.a2), u + cnn_off(4), u + cnn_off(5), A.a3, nullptr, desc,
         tiles_before, S);
     conv_out_kernel<<<(unsigned)ntiles, kTile, 0, st>>>(reinterpret_cast<const __nv_bfloat16 *>(A.a3),
@@ -381,11 +391,11 @@ cudaError_t cnn_backward(const CnnState &W, const uint16_t *feat, const CnnActs 
     bwd_out_kernel<<<(unsigned)((n3 + 255) / 256), 256, 0, st>>>(A.g, u + cnn_off(6), a3, A.dz3, desc, S, T);
     // layer 3
     wgrad_kernel<32, 32><<<wblocks, 256, 0, st>>>(A.dz3, a2, gd + cnn_off(4), gd + cnn_off(5), desc, S, T, tps, tpb);
-    conv32_kernel<32, float, true><<<(unsigned)ntiles, 256, 0, st>>>(A.dz3, W.flipped + 5120, nullptr, A.dz2, a2, desc,
+    conv32_kernel<32, float, true><<<(unsigned)ntiles, 128, 0, st>>>(A.dz3, W.flipped + 5120, nullptr, A.dz2, a2, desc,
                                                                      A.tiles_before, S);
     // layer 2
     wgrad_kernel<32, 32><<<wblocks, 256, 0, st>>>(A.dz2, a1, gd + cnn_off(2), gd + cnn_off(3), desc, S, T, tps, tpb);
-    conv32_kernel<32, float, true><<<(unsigned)ntiles, 256, 0, st>>>(A.dz2, W.flipped, nullptr, A.dz1, a1, desc,
+    conv32_kernel<32, float, true><<<(unsigned)ntiles, 128, 0, st>>>(A.dz2, W.flipped, nullptr, A.dz1, a1, desc,
                                                                      A.tiles_before, S);
     // layer 1
     wgrad_kernel<kFeatC, 32><<<wblocks, 256, 0, st>>>(A.dz1, x0, gd + cnn_off(0), gd + cnn_off(1), desc, S, T, tps,

@@ -154,6 +154,15 @@ union StageUnion {
     SliceStage<4> s4;
 };
 
+// Per-warp staging for one-group slices: (si, ei, cb0, cb1) of 32 runs as int4, and a
+// 32-bin histogram for counting differentiating samples.
+struct WarpStage {
+    StageUnion u;
+    int4 run[32];
+    uint4 lbl[32];  // up to 8 differentiating labels of each staged run (16-bit each)
+    int hist[32];
+};
+
 // Lower bound of v among the in-segment labels [si, ei) of a run whose first and last
 // in-segment labels are fi and la, starting the search at `from`.
 __device__ __forceinline__ int count_below(const uint16_t *__restrict__ lab, int si, int ei, int fi, int la,
@@ -173,6 +182,105 @@ __device__ __forceinline__ int count_below(const uint16_t *__restrict__ lab, int
 // [k0 + 32 q, k0 + 32 q + 32) distinguish the lanes, and each lane counts those below its
 // own k, by broadcast for up to kShflMax of them, else by a search in that short sorted
 // slice.  Empty runs are compacted away; the walk visits the runs in value order.
+// One-group (32-split) slice with int4 staging and histogram counting (the common tile).
+template <bool WIDE>
+__device__ void scan_slice1(const uint16_t *__restrict__ lab, const int32_t *__restrict__ rt, int U, int T, int lo,
+                            int hi, int k0, WarpStage &ws, uint64_t &g_out, int &nonempty) {
+    const int lane = threadIdx.x & 31;
+    const int k = k0 + lane, k1 = k0 + 32;
+    const uint32_t H = (uint32_t)(hi - lo);
+    const uint32_t a = (uint32_t)(k - lo);
+    uint32_t cl = 0, C = 0, mx32 = 0;
+    uint64_t mx = 0;
+    nonempty = 0;
+    ws.hist[lane] = 0;
+    __syncwarp();
+    for (int j0 = 0; j0 < U; j0 += 32) {
+        const int j = j0 + lane;
+        int si = 0, ei = 0, cb = 0, ce = 0;
+        if (j < U) {
+            const int a0 = __ldg(rt + j), b0 = __ldg(rt + j + 1);
+            const int f0 = __ldg(lab + a0), l0 = __ldg(lab + b0 - 1);
+            si = (f0 >= lo) ? a0 : (l0 < lo ? b0 : lower_bound_lab(lab, a0, b0, lo));
+            ei = (l0 < hi) ? b0 : (f0 >= hi ? a0 : lower_bound_lab(lab, si, b0, hi));
+            if (ei > si) {
+                const int fi = (si == a0) ? f0 : __ldg(lab + si);
+                const int la = (ei == b0) ? l0 : __ldg(lab + ei - 1);
+                const int c0 = count_below(lab, si, ei, fi, la, si, k0);
+                cb = c0 - si;
+                ce = count_below(lab, si, ei, fi, la, c0, k1) - si;
+            }
+        }
+        // prefetch the few labels that distinguish the lanes (independent loads across lanes)
+        uint32_t pk[4] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu};
+        const int Lr = ce - cb;
+        if (Lr > 0 && Lr <= kShflMax) {
+            const uint16_t *src = lab + si + cb;
+#pragma unroll
+            for (int q = 0; q < kShflMax; q++) {
+                const uint32_t v = q < Lr ? (uint32_t)__ldg(src + q) : 0xffffu;
+                pk[q >> 1] = (q & 1) ? ((pk[q >> 1] & 0xffffu) | (v << 16)) : ((pk[q >> 1] & 0xffff0000u) | v);
+            }
+        }
+        const unsigned ne = __ballot_sync(kFull, ei > si);
+        if (ei > si) {
+            const int pos = __popc(ne & lanemask_lt());
+            ws.run[pos] = make_int4(si, ei, cb, ce);
+            ws.lbl[pos] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        }
+        __syncwarp();
+        const int cnt = __popc(ne);
+        for (int r = 0; r < cnt; r++) {
+            const int4 q = ws.run[r];
+            C += (uint32_t)(q.y - q.x);
+            uint32_t add = (uint32_t)q.z;
+            const int L = q.w - q.z;
+            if (L > 0) {  // warp-uniform
+                const int sb = q.x + q.z;
+                if (L <= kShflMax) {
+                    // staged labels; unused slots hold 0xffff, above every k
+                    const uint4 lb4 = ws.lbl[r];
+                    const uint32_t w4[4] = {lb4.x, lb4.y, lb4.z, lb4.w};
+#pragma unroll
+                    for (int t = 0; t < 4; t++)
+                        add += (uint32_t)((int)(w4[t] & 0xffffu) < k) + (uint32_t)((int)(w4[t] >> 16) < k);
+                } else if (L <= 32) {
+                    // histogram of the slice's labels over the 32 lanes, then an exclusive scan
+                    const int bin = lane < L ? (int)__ldg(lab + sb + lane) - k0 : -1;
+                    if (bin >= 0) atomicAdd(&ws.hist[bin], 1);
+                    __syncwarp();
+                    const int hv = ws.hist[lane];
+                    int incl = hv;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(kFull, incl, o);
+                        if (lane >= o) incl += y;
+                    }
+                    add += (uint32_t)(incl - hv);
+                    __syncwarp();
+                    if (bin >= 0) ws.hist[bin] = 0;
+                    __syncwarp();
+                } else {
+                    add += (uint32_t)(lower_bound_lab(lab, sb, sb + L, k) - sb);
+                }
+            }
+            cl += add;
+            if (WIDE) {
+                const int64_t f = (int64_t)H * cl - (int64_t)a * C;
+                const uint64_t af = (uint64_t)(f < 0 ? -f : f);
+                mx = af > mx ? af : mx;
+            } else {
+                const int32_t f = (int32_t)(H * cl - a * C);
+                const uint32_t af = (uint32_t)(f < 0 ? -f : f);
+                mx32 = max(mx32, af);
+            }
+        }
+        nonempty += cnt;
+        __syncwarp();
+    }
+    g_out = WIDE ? mx : (uint64_t)mx32;
+}
+
 template <bool WIDE, int KPT>
 __device__ void scan_slice(const uint16_t *__restrict__ lab, const int32_t *__restrict__ rt, int U, int T, int lo,
                            int hi, int k0, SliceStage<KPT> &st, uint64_t (&g)[KPT], int &nonempty) {
@@ -553,11 +661,15 @@ __device__ __noinline__ void certify_segment(const RunParams &P, const SeriesDes
 // gets the result.
 template <bool WIDE, int KPT>
 __device__ void slice_best(const RunParams &P, const SeriesDesc &d, int lo, int hi, int k0, int kmin, int kmax,
-                           StageUnion &stage, int &bk, uint64_t &bg, int &nonempty) {
+                           WarpStage &stage, int &bk, uint64_t &bg, int &nonempty) {
     const int lane = threadIdx.x & 31;
     uint64_t g[KPT];
-    SliceStage<KPT> &st = *reinterpret_cast<SliceStage<KPT> *>(&stage);
-    scan_slice<WIDE, KPT>(P.lab + d.off, P.runs + d.run_base, d.nruns, d.T, lo, hi, k0, st, g, nonempty);
+    if constexpr (KPT == 1) {
+        scan_slice1<WIDE>(P.lab + d.off, P.runs + d.run_base, d.nruns, d.T, lo, hi, k0, stage, g[0], nonempty);
+    } else {
+        SliceStage<KPT> &st = *reinterpret_cast<SliceStage<KPT> *>(&stage.u);
+        scan_slice<WIDE, KPT>(P.lab + d.off, P.runs + d.run_base, d.nruns, d.T, lo, hi, k0, st, g, nonempty);
+    }
     bk = kNoK;
     bg = 0;
 #pragma unroll
@@ -574,9 +686,9 @@ __device__ void slice_best(const RunParams &P, const SeriesDesc &d, int lo, int 
 // Persistent kernel: every warp independently takes tickets from the queue and processes
 // one item per ticket.  No block-level synchronisation.
 __global__ void __launch_bounds__(kScanThreads, 4) queue_kernel(RunParams P, uint32_t epoch) {
-    __shared__ StageUnion s_stage[kScanThreads / 32];
+    __shared__ WarpStage s_stage[kScanThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    StageUnion &stage = s_stage[warp];
+    WarpStage &stage = s_stage[warp];
     const unsigned long long cap = P.q->cap;
     unsigned long long my_evals = 0;
 
@@ -625,7 +737,7 @@ __global__ void __launch_bounds__(kScanThreads, 4) queue_kernel(RunParams P, uin
             const int gn = __shfl_down_sync(kFull, gk, 1);
             uint64_t g = 0, ubm = 0;
             scan_grid(P.lab + d.off, P.runs + d.run_base, d.nruns, d.T, lo, hi, d.m, gk, lane + 1 < ng ? gn : gk,
-                      stage.s1, g, ubm, nonempty);
+                      stage.u.s1, g, ubm, nonempty);
             const uint64_t ub = (ubm + (uint64_t)d.m - 1) / (uint64_t)d.m;  // bound on g over the gap
             my_evals += (unsigned long long)ng * (unsigned long long)nonempty;
             CertRecord *rec = P.recs + it.rec;

@@ -9,8 +9,8 @@
 // per sample; otherwise values and 16-bit labels move separately.  The first read
 // also counts the first digit, and each pass counts the next one while it ranks.
 //
-// Within a 4096-sample tile, each warp ranks its 256 samples with match.any
-// (stable: item-major, then lane order), per-warp digit counts are scanned across
+// Within a 4096-sample tile, each warp ranks its 256 samples by digit-peer masks built
+// from eight ballots (stable: item-major, then lane order), per-warp digit counts are scanned across
 // warps, the tile is staged in shared memory in sorted order and written out so
 // that consecutive positions of a digit go to consecutive addresses; a running
 // per-digit base carries the order across tiles.  The last step writes the labels
@@ -53,10 +53,33 @@ __device__ void scan256(const uint32_t *s_in, uint32_t *s_out, uint32_t *s_tmp) 
     __syncthreads();
 }
 
-// Warp-aggregated shared-memory histogram increment (callers pass the valid-lane mask).
+// Lanes of vm holding the same 8-bit digit as this lane, from eight ballots (the result of
+// match.any, at a fraction of its cost).  Every lane of the warp must call it.
+__device__ __forceinline__ unsigned digit_peers(uint32_t dg, unsigned vm) {
+    unsigned peers = vm;
+#pragma unroll
+    for (int b = 0; b < 8; b++) {
+        const unsigned bal = __ballot_sync(kFull, (dg >> b) & 1u);
+        peers &= ((dg >> b) & 1u) ? bal : ~bal;
+    }
+    return peers;
+}
+
+// Warp-aggregated shared-memory histogram increment.  Every lane calls it; lanes outside
+// vm contribute nothing.
 __device__ __forceinline__ void hist_add(uint32_t *h, uint32_t dg, unsigned vm) {
-    const unsigned peers = __match_any_sync(vm, dg);
-    if ((int)(__ffs(peers) - 1) == (int)(threadIdx.x & 31)) atomicAdd(h + dg, (uint32_t)__popc(peers));
+    const unsigned peers = digit_peers(dg, vm);
+    const bool valid = (vm >> (threadIdx.x & 31)) & 1u;
+    if (valid && (int)(__ffs(peers) - 1) == (int)(threadIdx.x & 31)) atomicAdd(h + dg, (uint32_t)__popc(peers));
+}
+
+// e / m for 0 <= e < 2^30 by a single-precision reciprocal and an exact correction.
+__device__ __forceinline__ uint32_t div_step(uint32_t e, uint32_t m, float inv_m) {
+    uint32_t t = __float2uint_rz((float)e * inv_m);
+    const uint32_t r = t * m;
+    if (r > e) t -= (r - e + m - 1) / m;                // at most a couple of steps
+    else if (e - r >= m) t += (e - r) / m;
+    return t;
 }
 
 struct SortSmem {
@@ -80,6 +103,7 @@ template <bool COMP>
 __device__ void lsd_passes(SortSmem &sm, int passes, const uint32_t *__restrict__ in, int32_t N, int32_t m,
                            uint32_t *keyA, uint32_t *keyB, uint16_t *labA, uint16_t *labB) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const float inv_m = 1.0f / (float)m;
     for (int p = 0; p < passes; p++) {
         const int shift = 8 * p;
         const uint32_t *src_key = (p & 1) ? keyB : keyA;
@@ -96,39 +120,47 @@ __device__ void lsd_passes(SortSmem &sm, int passes, const uint32_t *__restrict_
             __syncwarp();
             uint32_t key[kSortItems], rk[kSortItems];
             uint16_t lb[kSortItems];
+            // all loads of the tile first, so they are in flight together
 #pragma unroll
             for (int it = 0; it < kSortItems; it++) {
                 const int e = tb + warp * (32 * kSortItems) + it * 32 + lane;
-                const bool valid = e < N;
                 key[it] = 0;
                 lb[it] = 0;
-                rk[it] = 0;
-                if (valid) {
+                if (e < N) {
                     if (p == 0) {
-                        const uint32_t v = __ldg(in + e);
-                        const uint32_t t = (uint32_t)(e / m);
-                        key[it] = COMP ? ((v << 16) | t) : v;
-                        lb[it] = (uint16_t)t;
+                        key[it] = __ldg(in + e);
                     } else {
                         key[it] = src_key[e];
                         if (!COMP) lb[it] = src_lab[e];
                     }
                 }
-                const unsigned vm = __ballot_sync(kFull, valid);
-                if (valid) {
-                    const uint32_t val = COMP ? key[it] >> 16 : key[it];
-                    const uint32_t dg = (val >> shift) & 255u;
-                    const unsigned peers = __match_any_sync(vm, dg);
-                    const int leader = __ffs(peers) - 1;
-                    uint32_t old = 0;
-                    if (lane == leader) {
-                        old = sm.wc[warp][dg];
-                        sm.wc[warp][dg] = old + (uint32_t)__popc(peers);
-                    }
-                    old = __shfl_sync(peers, old, leader);
-                    rk[it] = old + (uint32_t)__popc(peers & lanemask_lt());
-                    if (has_next) hist_add(sm.hist2, (val >> (shift + 8)) & 255u, vm);
+            }
+            if (p == 0) {
+#pragma unroll
+                for (int it = 0; it < kSortItems; it++) {
+                    const int e = tb + warp * (32 * kSortItems) + it * 32 + lane;
+                    const uint32_t t = div_step((uint32_t)min(e, N - 1), (uint32_t)m, inv_m);
+                    if (COMP) key[it] = (key[it] << 16) | t;
+                    lb[it] = (uint16_t)t;
                 }
+            }
+#pragma unroll
+            for (int it = 0; it < kSortItems; it++) {
+                const int e = tb + warp * (32 * kSortItems) + it * 32 + lane;
+                const bool valid = e < N;
+                const unsigned vm = __ballot_sync(kFull, valid);
+                const uint32_t val = COMP ? key[it] >> 16 : key[it];
+                const uint32_t dg = (val >> shift) & 255u;
+                const unsigned peers = digit_peers(dg, vm);
+                const int leader = valid ? __ffs(peers) - 1 : 0;
+                uint32_t old = 0;
+                if (valid && lane == leader) {
+                    old = sm.wc[warp][dg];
+                    sm.wc[warp][dg] = old + (uint32_t)__popc(peers);
+                }
+                old = __shfl_sync(kFull, old, leader);
+                rk[it] = old + (uint32_t)__popc(peers & lanemask_lt());
+                if (has_next) hist_add(sm.hist2, (val >> (shift + 8)) & 255u, vm);
                 __syncwarp();
             }
             __syncthreads();
@@ -201,11 +233,9 @@ sort_series_kernel(const uint32_t *__restrict__ samples, SeriesDesc *__restrict_
         const int i = b0 + tid;
         const bool valid = i < N;
         const unsigned vm = __ballot_sync(kFull, valid);
-        if (valid) {
-            const uint32_t v = __ldg(in + i);
-            vmax = max(vmax, v);
-            hist_add(sm.hist, v & 255u, vm);
-        }
+        const uint32_t v = valid ? __ldg(in + i) : 0u;
+        vmax = max(vmax, v);
+        hist_add(sm.hist, v & 255u, vm);
     }
     vmax = __reduce_max_sync(kFull, vmax);
     if (lane == 0) sm.tmp[warp] = vmax;
@@ -228,34 +258,57 @@ sort_series_kernel(const uint32_t *__restrict__ samples, SeriesDesc *__restrict_
     else
         lsd_passes<false>(sm, passes, in, N, m, kA, kB, lA, lB);
 
-    // ---- run table and final labels (into labA)
+    // ---- run table and final labels (into labA), 8 consecutive samples per thread per round
     const uint32_t *fk = (passes & 1) ? kB : kA;
     const uint16_t *flab = (passes & 1) ? lB : lA;
     int32_t *rt = runs + d.run_base;
     uint32_t count = 0;
-    for (int tb = 0; tb < N; tb += kSortThreads) {
-        const int i = tb + tid;
-        bool flag = false;
-        if (i < N) {
-            const uint32_t k2 = fk[i];
-            const uint32_t v = comp ? k2 >> 16 : k2;
-            const uint32_t vp = i > 0 ? (comp ? fk[i - 1] >> 16 : fk[i - 1]) : ~v;
-            flag = (i == 0) || v != vp;
-            if (comp)
-                lA[i] = (uint16_t)(k2 & 0xffffu);
-            else if (passes & 1)
-                lA[i] = flab[i];
+    constexpr int kRunItems = 8;
+    for (int tb = 0; tb < N; tb += kSortThreads * kRunItems) {
+        const int i0 = tb + tid * kRunItems;
+        uint32_t v[kRunItems + 1];
+#pragma unroll
+        for (int q = 0; q <= kRunItems; q++) {
+            const int i = i0 + q - 1;
+            const uint32_t k2 = (i >= 0 && i < N) ? fk[i] : 0u;
+            v[q] = comp ? k2 >> 16 : k2;
+            if (q > 0 && i < N) {
+                if (comp)
+                    lA[i] = (uint16_t)(k2 & 0xffffu);
+                else if (passes & 1)
+                    lA[i] = flab[i];
+            }
         }
-        const unsigned b = __ballot_sync(kFull, flag);
-        if (lane == 0) sm.tmp[warp] = (uint32_t)__popc(b);
+        uint32_t fl = 0;  // bit q: sample i0 + q starts a run
+#pragma unroll
+        for (int q = 0; q < kRunItems; q++) {
+            const int i = i0 + q;
+            if (i < N && (i == 0 || v[q + 1] != v[q])) fl |= 1u << q;
+        }
+        const uint32_t mine = (uint32_t)__popc(fl);
+        uint32_t incl = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) sm.tmp[warp] = incl;
         __syncthreads();
         uint32_t before = 0, total = 0;
-        for (int w = 0; w < kSortWarps; w++) {
-            const uint32_t c = sm.tmp[w];
-            if (w < warp) before += c;
-            total += c;
+        if (lane < kSortWarps) {
+            const uint32_t c = sm.tmp[lane];
+            before = lane < warp ? c : 0;
+            total = c;
         }
-        if (flag) rt[count + before + (uint32_t)__popc(b & lanemask_lt())] = i;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            before += __shfl_xor_sync(kFull, before, o);
+            total += __shfl_xor_sync(kFull, total, o);
+        }
+        uint32_t pos = count + before + incl - mine;
+#pragma unroll
+        for (int q = 0; q < kRunItems; q++)
+            if (fl & (1u << q)) rt[pos++] = i0 + q;
         count += total;
         __syncthreads();
     }

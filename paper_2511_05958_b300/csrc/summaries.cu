@@ -87,7 +87,7 @@ __device__ void summarise_step(const uint32_t *__restrict__ row, int m, float lm
     if (lane < kFeatC) out[lane] = __float2bfloat16_rn(f);
 }
 
-__global__ void __launch_bounds__(256) summaries_kernel(const uint32_t *__restrict__ samples,
+__global__ void __launch_bounds__(256, 4) summaries_kernel(const uint32_t *__restrict__ samples,
                                                         const SeriesDesc *__restrict__ desc,
                                                         __nv_bfloat16 *__restrict__ feat) {
     const int64_t s = blockIdx.x;
