@@ -71,6 +71,10 @@ extern "C" {
 #define MT4G_OPT_HALF_WIDTH 5    /* learned mode: window half width in steps (default 16) */
 #define MT4G_OPT_CONF_MIN_PPM 6  /* learned mode: series whose window mass is below this (in
                                     millionths, default 900000) take the full scan */
+#define MT4G_OPT_GRAPH 7         /* 1: mt4g_ks_scan / mt4g_ks_segment run as one CUDA-graph launch.
+                                    The first call with given arguments (pointers, sizes, host
+                                    table contents, options, weights) is captured; identical calls
+                                    replay it.  Stage timing is not recorded for graph calls. */
 
 typedef struct mt4g_ctx mt4g_ctx;
 
@@ -200,6 +204,28 @@ int mt4g_propose(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets,
                  int32_t n_win, int32_t half_width, int32_t *win_center, float *conf, void *cuda_stream);
 
 /*
+ * Scan-tile autotuner (no counterpart in the paper).  The work queue scans each segment in
+ * warp items of 32, 64 or 128 splits (the tile).  mt4g_autotune times mt4g_ks_scan with each
+ * tile on up to 256 series of every (floor log2 T, floor log2 m) bucket present in the batch
+ * (copied into a temporary buffer) and keeps the fastest tile per bucket in the context;
+ * later calls use it for series of that bucket (default 32 splits).  Synchronises the
+ * stream.  The table can be written to and read from a text file; mt4g_autotune_get returns
+ * the tile (1, 2 or 4 groups of 32) used for a shape.
+ */
+int mt4g_autotune(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets, const int32_t *steps, int64_t S,
+                  void *cuda_stream);
+int mt4g_autotune_save(mt4g_ctx *ctx, const char *path);
+int mt4g_autotune_load(mt4g_ctx *ctx, const char *path);
+int mt4g_autotune_get(mt4g_ctx *ctx, int32_t T, int32_t m);
+
+/* Critical value of D at level alpha for samples of n_left and n_right values (Eq. 1, with
+ * the minus sign its printed radicand lost and the natural log):
+ *   d_alpha = sqrt(-1/2 ln(alpha / 2) (n_left + n_right) / (n_left n_right)),
+ * the inversion of the first term 2 exp(-2 lambda^2) = alpha of the Kolmogorov series.
+ * Returns -1 for alpha outside (0, 1) or a sample size below 1.  Host function. */
+double mt4g_critical_value(double alpha, int64_t n_left, int64_t n_right);
+
+/*
  * Allocation-free variant of mt4g_ks_scan (no counterpart in the paper).
  *
  * For callers that cannot allocate device (or host) memory: code running inside a memory
@@ -239,6 +265,11 @@ int mt4g_ks_scan_noalloc(const uint32_t *samples, const int64_t *offsets, const 
  */
 int mt4g_stage_times(mt4g_ctx *ctx, double *ms_out, int32_t max_calls);
 int mt4g_last_work(mt4g_ctx *ctx, int64_t *evals);
+/* Failure-detection self-test (no counterpart in the paper): runs the work-queue kernel
+ * over a queue that claims one pending item and never publishes it, with every wait bounded
+ * by limit_ns (<= 2e9).  mt4g_wait() must then return MT4G_ETIMEOUT, and the context stays
+ * usable for the next call. */
+int mt4g_selftest_wait_timeout(mt4g_ctx *ctx, int64_t limit_ns, void *cuda_stream);
 /* After mt4g_wait() on a learned call: out[0] = segments decided by their probe group,
  * out[1] = segments that needed refinement slices, out[2] = probe groups pushed. */
 int mt4g_learned_stats(mt4g_ctx *ctx, int64_t *out);

@@ -24,6 +24,7 @@ OPT_SCAN_KPT = 3
 OPT_WINDOWS = 4
 OPT_HALF_WIDTH = 5
 OPT_CONF_MIN_PPM = 6
+OPT_GRAPH = 7
 MAX_STEPS = 32768
 FEAT_CHANNELS = 18
 CNN_PARAMS = 13377
@@ -63,6 +64,13 @@ def load_library():
     L.mt4g_ks_segment.argtypes = [vp, vp, vp, vp, i64, dbl, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp]
     L.mt4g_learned_stats.argtypes = [vp, vp]
     L.mt4g_ks_scan_noalloc.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp, vp]
+    L.mt4g_selftest_wait_timeout.argtypes = [vp, i64, vp]
+    L.mt4g_autotune.argtypes = [vp, vp, vp, vp, i64, vp]
+    L.mt4g_autotune_save.argtypes = [vp, ctypes.c_char_p]
+    L.mt4g_autotune_load.argtypes = [vp, ctypes.c_char_p]
+    L.mt4g_autotune_get.argtypes = [vp, i32, i32]
+    L.mt4g_critical_value.argtypes = [dbl, i64, i64]
+    L.mt4g_critical_value.restype = dbl
     L.mt4g_stage_times.argtypes = [vp, vp, i32]
     L.mt4g_last_work.argtypes = [vp, vp]
     L.mt4g_summaries.argtypes = [vp, vp, vp, vp, i64, vp, vp]
@@ -85,7 +93,8 @@ def exported_symbols():
             "mt4g_ks_scan", "mt4g_ks_segment", "mt4g_stage_times", "mt4g_last_work",
             "mt4g_summaries", "mt4g_cnn_init", "mt4g_cnn_get_params", "mt4g_cnn_set_params", "mt4g_cnn_save",
             "mt4g_cnn_load", "mt4g_cnn_forward", "mt4g_cnn_grads", "mt4g_cnn_train_step", "mt4g_propose",
-            "mt4g_learned_stats", "mt4g_ks_scan_noalloc"]
+            "mt4g_learned_stats", "mt4g_ks_scan_noalloc", "mt4g_selftest_wait_timeout", "mt4g_critical_value",
+            "mt4g_autotune", "mt4g_autotune_save", "mt4g_autotune_load", "mt4g_autotune_get"]
 
 
 class ScanResult(NamedTuple):
@@ -183,6 +192,30 @@ class Engine:
         self._check(self._L.mt4g_learned_stats(self._h, v.ctypes.data_as(ctypes.c_void_p)))
         return {"certified": int(v[0]), "refined": int(v[1]), "probe_groups": int(v[2])}
 
+    def selftest_wait_timeout(self, limit_ns: int = 10_000_000, stream=None) -> int:
+        """Run the queue kernel on a queue whose pending item never comes; returns mt4g_wait()'s code."""
+        self._check(self._L.mt4g_selftest_wait_timeout(self._h, int(limit_ns), _stream_handle(stream)))
+        return self.wait()
+
+    def autotune(self, samples, offsets, steps, stream=None):
+        """Time each scan tile per (log2 T, log2 m) bucket of the batch and keep the fastest."""
+        offsets, steps = _host_tables(offsets, steps)
+        self._check(self._L.mt4g_autotune(self._h, _dev_ptr(samples, "samples"), offsets.ctypes.data_as(ctypes.c_void_p),
+                                          steps.ctypes.data_as(ctypes.c_void_p), steps.shape[0],
+                                          _stream_handle(stream)))
+
+    def autotune_save(self, path: str):
+        self._check(self._L.mt4g_autotune_save(self._h, os.fsencode(path)))
+
+    def autotune_load(self, path: str):
+        self._check(self._L.mt4g_autotune_load(self._h, os.fsencode(path)))
+
+    def autotune_get(self, T: int, m: int) -> int:
+        v = int(self._L.mt4g_autotune_get(self._h, int(T), int(m)))
+        if v < 0:
+            self._check(v)
+        return v
+
     def last_work(self) -> int:
         """(split, distinct value) pairs evaluated by the last call (valid after wait())."""
         v = np.zeros(1, np.int64)
@@ -232,6 +265,11 @@ class Engine:
             if status not in (OK, ECAPACITY):
                 self._check(status)
         return out._replace(rc=status)
+
+
+def critical_value(alpha: float, n_left: int, n_right: int) -> float:
+    """Eq. 1 critical value of D (host computation in the library)."""
+    return float(load_library().mt4g_critical_value(float(alpha), int(n_left), int(n_right)))
 
 
 def feature_rows(steps) -> int:

@@ -2,8 +2,10 @@
 //   (reduce+rank for Eq. 2 mode) -> per-series radix sort + run table ->
 //   persistent work-queue kernel (scan, p-value, segmentation) -> collect.
 #include <algorithm>
+#include <map>
 #include <cstdarg>
 #include <cstdio>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <numeric>
@@ -31,6 +33,7 @@ struct mt4g_ctx {
     bool last_enqueued = false;  // the most recent call enqueued work (its status is in h_hdr)
 
     int32_t forced_kpt = 0;  // 0: per-series choice; 1, 2, 4: every series
+    std::map<std::pair<int, int>, int32_t> tune;  // (floor log2 T, floor log2 m) -> scan tile
     int32_t n_win = 3;       // learned proposals: windows per series
     int32_t half = 16;       // window half width
     float conf_min = 0.9f;   // below: the series takes the plain scan
@@ -51,6 +54,17 @@ struct mt4g_ctx {
     cudaEvent_t ev[kTimingRing][kMarks] = {};
     int ring_pos = 0;
     int ring_count = 0;
+
+    // CUDA-graph replay of identical calls (MT4G_OPT_GRAPH)
+    bool use_graph = false;
+    bool capturing = false;       // inside a capture: no host syncs, staging from graph_pin
+    void *graph_pin = nullptr;    // pinned staging owned by the captured graph
+    size_t graph_pin_bytes = 0, graph_pin_off = 0;
+    cudaGraphExec_t graph_exec = nullptr;
+    uint64_t graph_key = 0;
+    cudaStream_t graph_stream = nullptr;        // graphs are captured and launched here
+    cudaEvent_t graph_in = nullptr, graph_out = nullptr;  // joins with the caller's stream
+    long long cnn_version = 0;    // bumped whenever the weights change
 
     // work-queue ready flags carry an epoch so they need no clearing between calls
     uint32_t call_counter = 0;
@@ -161,18 +175,26 @@ size_t carve(void *base, const Plan &P, Buffers &B, size_t *ready_off) {
     return c.off + 256;
 }
 
-// Record stage boundary `i` of the current call when stage timing is on.
+// Record stage boundary `i` of the current call when stage timing is on (not in graphs).
 void mark(mt4g_ctx *ctx, int i, cudaStream_t st) {
-    if (ctx->timing) cudaEventRecord(ctx->ev[ctx->ring_pos][i], st);
+    if (ctx->timing && !ctx->capturing) cudaEventRecord(ctx->ev[ctx->ring_pos][i], st);
 }
 
 // Scan tile for a series: split groups of 32 per warp work item.  A forced value
 // (MT4G_OPT_SCAN_KPT) wins; otherwise the autotuned table, else a size heuristic.
+int ilog2(int64_t v) {
+    int b = 0;
+    while (v > 1) {
+        v >>= 1;
+        b++;
+    }
+    return b;
+}
+
 int32_t pick_kpt(const mt4g_ctx *ctx, int32_t T, int32_t m) {
     if (ctx->forced_kpt) return ctx->forced_kpt;
-    (void)T;
-    (void)m;
-    return 1;
+    const auto it = ctx->tune.find({ilog2(T), ilog2(m)});
+    return it == ctx->tune.end() ? 1 : it->second;
 }
 
 // Validate the host tables and build the per-call plan.
@@ -269,7 +291,12 @@ int make_plan(mt4g_ctx *ctx, const int64_t *offsets, const int32_t *steps, int64
 
 int ensure_workspace(mt4g_ctx *ctx, size_t bytes) {
     if (bytes <= ctx->ws_bytes) return MT4G_OK;
+    if (ctx->capturing) return fail(ctx, MT4G_ECUDA, "workspace growth during graph capture");
     if (ctx->have_last) CUDA_TRY(ctx, cudaStreamSynchronize(ctx->last_stream));
+    if (ctx->graph_exec) {  // the captured graph points into the old workspace
+        cudaGraphExecDestroy(ctx->graph_exec);
+        ctx->graph_exec = nullptr;
+    }
     if (ctx->ws) cudaFree(ctx->ws);
     ctx->ws = nullptr;
     ctx->ws_bytes = 0;
@@ -281,6 +308,7 @@ int ensure_workspace(mt4g_ctx *ctx, size_t bytes) {
 }
 
 int ensure_pinned(mt4g_ctx *ctx, size_t bytes) {
+    if (ctx->capturing) return fail(ctx, MT4G_ECUDA, "pinned staging during graph capture");
     CUDA_TRY(ctx, cudaEventSynchronize(ctx->pin_free));
     if (bytes <= ctx->pin_bytes) return MT4G_OK;
     if (ctx->pin) cudaFreeHost(ctx->pin);
@@ -292,6 +320,28 @@ int ensure_pinned(mt4g_ctx *ctx, size_t bytes) {
     return MT4G_OK;
 }
 
+// Host staging for uploads: the context's pinned buffer (after the previous uploads out of
+// it completed), or, while a graph is being captured, a slice of the graph's own buffer
+// (its contents must stay valid for every replay).
+unsigned char *stage_alloc(mt4g_ctx *ctx, size_t bytes, int *rc) {
+    *rc = MT4G_OK;
+    if (ctx->capturing) {
+        const size_t at = (ctx->graph_pin_off + 255) & ~(size_t)255;
+        if (at + bytes > ctx->graph_pin_bytes) {
+            *rc = fail(ctx, MT4G_ECUDA, "graph staging buffer too small");
+            return nullptr;
+        }
+        ctx->graph_pin_off = at + bytes;
+        return (unsigned char *)ctx->graph_pin + at;
+    }
+    *rc = ensure_pinned(ctx, bytes);
+    return *rc ? nullptr : (unsigned char *)ctx->pin;
+}
+
+cudaError_t staged(mt4g_ctx *ctx, cudaStream_t st) {
+    return ctx->capturing ? cudaSuccess : cudaEventRecord(ctx->pin_free, st);
+}
+
 // Everything a call enqueues up to (and including) the work-queue kernel.
 int enqueue_pipeline(mt4g_ctx *ctx, const uint32_t *samples, Plan &P, RunParams &R, Buffers &B, cudaStream_t st) {
     size_t ready_off = 0;
@@ -300,13 +350,18 @@ int enqueue_pipeline(mt4g_ctx *ctx, const uint32_t *samples, Plan &P, RunParams 
     if (rc) return rc;
     carve(ctx->ws, P, B, &ready_off);
 
-    // epoch of this call's ready flags; clear them when the layout changed or the epoch wraps
-    ctx->call_counter++;
-    uint32_t e = ctx->call_counter & 0x7fff;
-    const bool fresh = ready_off != ctx->ready_off || P.cap > ctx->ready_cap || e == 0;
-    if (e == 0) {
+    // epoch of this call's ready flags; clear them when the layout changed or the epoch wraps.
+    // A captured graph clears them on every replay and uses a fixed epoch.
+    uint32_t e = 0x7fff;
+    bool fresh = true;
+    if (!ctx->capturing) {
         ctx->call_counter++;
         e = ctx->call_counter & 0x7fff;
+        fresh = ready_off != ctx->ready_off || P.cap > ctx->ready_cap || e == 0;
+        if (e == 0) {
+            ctx->call_counter++;
+            e = ctx->call_counter & 0x7fff;
+        }
     }
     const uint32_t epoch = e << 16;
     if (fresh) {
@@ -323,9 +378,9 @@ int enqueue_pipeline(mt4g_ctx *ctx, const uint32_t *samples, Plan &P, RunParams 
     const size_t bytes_order = P.S * sizeof(int32_t);
     const size_t bytes_items = P.S * sizeof(int32_t);   // qorder
     const size_t bytes_ready = P.S * sizeof(int64_t);   // item_base
-    rc = ensure_pinned(ctx, bytes_hdr + bytes_desc + bytes_raw + bytes_order + bytes_items + bytes_ready + 64);
+    char *h = (char *)stage_alloc(ctx, bytes_hdr + bytes_desc + bytes_raw + bytes_order + bytes_items + bytes_ready + 64,
+                                  &rc);
     if (rc) return rc;
-    char *h = (char *)ctx->pin;
     QueueHeader hq{};
     hq.head = 0;
     hq.tail = P.learned ? 0 : n_items;
@@ -359,7 +414,7 @@ int enqueue_pipeline(mt4g_ctx *ctx, const uint32_t *samples, Plan &P, RunParams 
     if (bytes_items) CUDA_TRY(ctx, cudaMemcpyAsync(B.qorder, h + o_items, bytes_items, cudaMemcpyHostToDevice, st));
     if (bytes_ready)
         CUDA_TRY(ctx, cudaMemcpyAsync(B.item_base, h + o_ready, bytes_ready, cudaMemcpyHostToDevice, st));
-    CUDA_TRY(ctx, cudaEventRecord(ctx->pin_free, st));
+    CUDA_TRY(ctx, staged(ctx, st));
     if (!P.learned)
         CUDA_TRY(ctx, launch_init_items(B.desc, B.qorder, B.item_base, P.S, P.min_seg, B.items, B.ready, B.gcount,
                                         epoch, st));
@@ -396,7 +451,7 @@ int enqueue_proposals(mt4g_ctx *ctx, const uint32_t *samples, Plan &P, Buffers &
 
 int finish_call(mt4g_ctx *ctx, Buffers &B, cudaStream_t st) {
     mark(ctx, 5, st);
-    if (ctx->timing) {
+    if (ctx->timing && !ctx->capturing) {
         ctx->ring_pos = (ctx->ring_pos + 1) % mt4g_ctx::kTimingRing;
         ctx->ring_count = std::min(ctx->ring_count + 1, mt4g_ctx::kTimingRing);
     }
@@ -452,6 +507,14 @@ void mt4g_destroy(mt4g_ctx *c) {
     }
     if (c->ws) cudaFree(c->ws);
     if (c->cnn_ws) cudaFree(c->cnn_ws);
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph_pin) cudaFreeHost(c->graph_pin);
+    if (c->graph_stream) {
+        cudaStreamSynchronize(c->graph_stream);
+        cudaStreamDestroy(c->graph_stream);
+        cudaEventDestroy(c->graph_in);
+        cudaEventDestroy(c->graph_out);
+    }
     if (c->cnn_alloc) cudaFree(c->cnn.master);
     if (c->pin) cudaFreeHost(c->pin);
     if (c->h_hdr) cudaFreeHost(c->h_hdr);
@@ -481,6 +544,10 @@ int mt4g_set_option(mt4g_ctx *c, int option, int64_t value) {
         if (value != 0 && value != 1 && value != 2 && value != 4)
             return fail(c, MT4G_EINVAL, "scan tile must be 0 (automatic), 1, 2 or 4");
         c->forced_kpt = (int32_t)value;
+        return MT4G_OK;
+    }
+    if (option == MT4G_OPT_GRAPH) {
+        c->use_graph = value != 0;
         return MT4G_OK;
     }
     if (option == MT4G_OPT_WINDOWS) {
@@ -519,11 +586,10 @@ int mt4g_wait(mt4g_ctx *c) {
     return MT4G_OK;
 }
 
-int mt4g_ks_scan(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets, const int32_t *steps, int64_t S,
-                 int32_t mode, int32_t *k_out, int64_t *dnum_out, int64_t *dden_out, double *p_out,
-                 void *cuda_stream) {
-    int rc = begin_call(ctx);
-    if (rc) return rc;
+static int scan_body(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets, const int32_t *steps,
+                     int64_t S, int32_t mode, int32_t *k_out, int64_t *dnum_out, int64_t *dden_out, double *p_out,
+                     void *cuda_stream) {
+    int rc = MT4G_OK;
     if (S > 0 && (!samples || !k_out || !dnum_out || !dden_out || !p_out))
         return fail(ctx, MT4G_EINVAL, "NULL device pointer");
     Plan P;
@@ -547,11 +613,11 @@ int mt4g_ks_scan(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets,
     return finish_call(ctx, B, st);
 }
 
-int mt4g_ks_segment(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets, const int32_t *steps, int64_t S,
-                    double alpha, int32_t min_seg, int32_t max_cp, int32_t mode, int32_t *cp_count, int32_t *cp_idx,
-                    int64_t *dnum, int64_t *dden, double *p, int32_t *fallback, void *cuda_stream) {
-    int rc = begin_call(ctx);
-    if (rc) return rc;
+static int segment_body(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets, const int32_t *steps,
+                        int64_t S, double alpha, int32_t min_seg, int32_t max_cp, int32_t mode, int32_t *cp_count,
+                        int32_t *cp_idx, int64_t *dnum, int64_t *dden, double *p, int32_t *fallback,
+                        void *cuda_stream) {
+    int rc = MT4G_OK;
     if (!(alpha > 0.0 && alpha < 1.0)) return fail(ctx, MT4G_EINVAL, "alpha must be in (0, 1)");
     if (max_cp < 0) return fail(ctx, MT4G_EINVAL, "max_cp must be >= 0");
     if (S > 0 && (!samples || !cp_count || (max_cp > 0 && (!cp_idx || !dnum || !dden || !p))))
@@ -591,6 +657,169 @@ int mt4g_ks_segment(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offse
     if (fallback)
         CUDA_TRY(ctx, cudaMemcpyAsync(fallback, B.fallback, P.S * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
     return finish_call(ctx, B, st);
+}
+
+
+}  // extern "C"
+
+namespace {
+
+uint64_t fnv1a(uint64_t h, const void *p, size_t n) {
+    const unsigned char *b = (const unsigned char *)p;
+    for (size_t i = 0; i < n; i++) h = (h ^ b[i]) * 0x100000001b3ULL;
+    return h;
+}
+
+template <class T>
+uint64_t fnv_val(uint64_t h, const T &v) {
+    return fnv1a(h, &v, sizeof(T));
+}
+
+// Run `body` directly, or (MT4G_OPT_GRAPH) as one CUDA-graph launch: a call identical to
+// the captured one (same key) replays it; otherwise `presize` grows every buffer first,
+// then the call is captured with no host synchronisation inside and launched.
+template <class Presize, class Body>
+int run_maybe_graph(mt4g_ctx *ctx, uint64_t key, size_t pin_bytes, cudaStream_t user_st, Presize &&presize,
+                    Body &&body) {
+    if (!ctx->use_graph) return body(user_st);
+    // the caller's stream may be the legacy default stream, which cannot be captured: capture
+    // and launch on the context's own stream, ordered after and before the caller's work
+    if (!ctx->graph_stream) {
+        CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->graph_stream, cudaStreamNonBlocking));
+        CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->graph_in, cudaEventDisableTiming));
+        CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->graph_out, cudaEventDisableTiming));
+    }
+    cudaStream_t st = ctx->graph_stream;
+    CUDA_TRY(ctx, cudaEventRecord(ctx->graph_in, user_st));
+    CUDA_TRY(ctx, cudaStreamWaitEvent(st, ctx->graph_in, 0));
+    if (ctx->graph_exec && ctx->graph_key == key) {
+        CUDA_TRY(ctx, cudaGraphLaunch(ctx->graph_exec, st));
+    } else {
+        if (ctx->have_last) CUDA_TRY(ctx, cudaStreamSynchronize(ctx->last_stream));
+        if (ctx->graph_exec) {
+            cudaGraphExecDestroy(ctx->graph_exec);
+            ctx->graph_exec = nullptr;
+        }
+        int rc = presize();
+        if (rc) return rc;
+        if (pin_bytes > ctx->graph_pin_bytes) {
+            if (ctx->graph_pin) cudaFreeHost(ctx->graph_pin);
+            ctx->graph_pin = nullptr;
+            ctx->graph_pin_bytes = 0;
+            CUDA_TRY(ctx, cudaMallocHost(&ctx->graph_pin, pin_bytes));
+            ctx->graph_pin_bytes = pin_bytes;
+        }
+        ctx->graph_pin_off = 0;
+        CUDA_TRY(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        ctx->capturing = true;
+        rc = body(st);
+        ctx->capturing = false;
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(st, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return fail(ctx, MT4G_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+        const cudaError_t ei = cudaGraphInstantiate(&ctx->graph_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) {
+            ctx->graph_exec = nullptr;
+            return fail(ctx, MT4G_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(ei));
+        }
+        ctx->graph_key = key;
+        CUDA_TRY(ctx, cudaGraphLaunch(ctx->graph_exec, st));
+    }
+    CUDA_TRY(ctx, cudaEventRecord(ctx->graph_out, st));
+    CUDA_TRY(ctx, cudaStreamWaitEvent(user_st, ctx->graph_out, 0));
+    ctx->ready_off = (size_t)-1;  // a later direct call clears the flags the graph used
+    ctx->last_stream = user_st;
+    ctx->have_last = true;
+    ctx->last_enqueued = true;
+    return MT4G_OK;
+}
+
+uint64_t call_key(const mt4g_ctx *ctx, int entry, const void *samples, const int64_t *offsets, const int32_t *steps,
+                  int64_t S, int32_t mode, double alpha, int32_t min_seg, int32_t max_cp, const void *const *outs,
+                  int n_outs, void *stream) {
+    uint64_t h = 0xcbf29ce484222325ULL;
+    h = fnv_val(h, entry);
+    h = fnv_val(h, samples);
+    h = fnv_val(h, S);
+    h = fnv_val(h, mode);
+    h = fnv_val(h, alpha);
+    h = fnv_val(h, min_seg);
+    h = fnv_val(h, max_cp);
+    h = fnv_val(h, stream);
+    h = fnv_val(h, ctx->n_win);
+    h = fnv_val(h, ctx->half);
+    h = fnv_val(h, ctx->conf_min);
+    h = fnv_val(h, ctx->forced_kpt);
+    h = fnv_val(h, ctx->cnn_version);
+    for (int i = 0; i < n_outs; i++) h = fnv_val(h, outs[i]);
+    if (S > 0 && offsets && steps) {
+        h = fnv1a(h, offsets, (size_t)(S + 1) * sizeof(int64_t));
+        h = fnv1a(h, steps, (size_t)S * sizeof(int32_t));
+    }
+    return h;
+}
+
+size_t graph_pin_need(int64_t S) { return (size_t)S * 256 + 8192; }
+
+int presize_cnn(mt4g_ctx *ctx, int64_t rows, int64_t S);  // proposal workspace (defined below)
+
+int presize_for(mt4g_ctx *ctx, const int64_t *offsets, const int32_t *steps, int64_t S, int32_t mode,
+                int32_t min_seg) {
+    if (S <= 0) return MT4G_OK;
+    Plan P;
+    int rc = make_plan(ctx, offsets, steps, S, mode, min_seg, P);
+    if (rc) return rc;
+    Buffers B;
+    size_t ready_off = 0;
+    rc = ensure_workspace(ctx, carve(nullptr, P, B, &ready_off));
+    if (rc) return rc;
+    if (mode == MT4G_MODE_LEARNED) rc = presize_cnn(ctx, P.sumT + 4 * S, S);
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mt4g_ks_scan(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets, const int32_t *steps, int64_t S,
+                 int32_t mode, int32_t *k_out, int64_t *dnum_out, int64_t *dden_out, double *p_out,
+                 void *cuda_stream) {
+    int rc = begin_call(ctx);
+    if (rc) return rc;
+    if (mode == MT4G_MODE_LEARNED) return fail(ctx, MT4G_EINVAL, "mt4g_ks_scan has no learned mode");
+    const void *outs[4] = {k_out, dnum_out, dden_out, p_out};
+    const uint64_t key = ctx->use_graph ? call_key(ctx, 1, samples, offsets, steps, S, mode, 0.0, 1, 0, outs, 4,
+                                                   cuda_stream)
+                                        : 0;
+    return run_maybe_graph(
+        ctx, key, graph_pin_need(S), (cudaStream_t)cuda_stream,
+        [&] { return presize_for(ctx, offsets, steps, S, mode, 1); },
+        [&](cudaStream_t s) {
+            return scan_body(ctx, samples, offsets, steps, S, mode, k_out, dnum_out, dden_out, p_out, (void *)s);
+        });
+}
+
+int mt4g_ks_segment(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets, const int32_t *steps, int64_t S,
+                    double alpha, int32_t min_seg, int32_t max_cp, int32_t mode, int32_t *cp_count, int32_t *cp_idx,
+                    int64_t *dnum, int64_t *dden, double *p, int32_t *fallback, void *cuda_stream) {
+    int rc = begin_call(ctx);
+    if (rc) return rc;
+    const void *outs[6] = {cp_count, cp_idx, dnum, dden, p, fallback};
+    const uint64_t key = ctx->use_graph ? call_key(ctx, 2, samples, offsets, steps, S, mode, alpha, min_seg, max_cp,
+                                                   outs, 6, cuda_stream)
+                                        : 0;
+    return run_maybe_graph(
+        ctx, key, graph_pin_need(S), (cudaStream_t)cuda_stream,
+        [&] { return presize_for(ctx, offsets, steps, S, mode, min_seg); },
+        [&](cudaStream_t s) {
+            return segment_body(ctx, samples, offsets, steps, S, alpha, min_seg, max_cp, mode, cp_count, cp_idx, dnum,
+                                dden, p, fallback, (void *)s);
+        });
 }
 
 int mt4g_stage_times(mt4g_ctx *c, double *ms_out, int32_t max_calls) {
@@ -675,8 +904,21 @@ size_t carve_cnn(void *base, int64_t rows, int64_t S, bool training, bool own_fe
 
 int ensure_cnn_ws(mt4g_ctx *c, size_t bytes) {
     if (bytes <= c->cnn_ws_bytes) return MT4G_OK;
+    if (c->capturing) return fail(c, MT4G_ECUDA, "workspace growth during graph capture");
     if (c->have_last) CUDA_TRY(c, cudaStreamSynchronize(c->last_stream));
+    if (c->graph_exec) {
+        cudaGraphExecDestroy(c->graph_exec);
+        c->graph_exec = nullptr;
+    }
     if (c->cnn_ws) cudaFree(c->cnn_ws);
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph_pin) cudaFreeHost(c->graph_pin);
+    if (c->graph_stream) {
+        cudaStreamSynchronize(c->graph_stream);
+        cudaStreamDestroy(c->graph_stream);
+        cudaEventDestroy(c->graph_in);
+        cudaEventDestroy(c->graph_out);
+    }
     c->cnn_ws = nullptr;
     c->cnn_ws_bytes = 0;
     const size_t want = bytes + bytes / 8;
@@ -691,15 +933,15 @@ int upload_cnn_tables(mt4g_ctx *c, const std::vector<SeriesDesc> &desc, CnnBuffe
     std::vector<int64_t> tb;
     *ntiles = cnn_tiles(desc, tb);
     const size_t S = desc.size();
-    int rc = ensure_pinned(c, S * (sizeof(SeriesDesc) + sizeof(int64_t)) + 64);
+    int rc = MT4G_OK;
+    char *h = (char *)stage_alloc(c, S * (sizeof(SeriesDesc) + sizeof(int64_t)) + 64, &rc);
     if (rc) return rc;
-    char *h = (char *)c->pin;
     memcpy(h, desc.data(), S * sizeof(SeriesDesc));
     memcpy(h + S * sizeof(SeriesDesc), tb.data(), S * sizeof(int64_t));
     CUDA_TRY(c, cudaMemcpyAsync(B.desc, h, S * sizeof(SeriesDesc), cudaMemcpyHostToDevice, st));
     CUDA_TRY(c, cudaMemcpyAsync(B.tiles_before, h + S * sizeof(SeriesDesc), S * sizeof(int64_t),
                                 cudaMemcpyHostToDevice, st));
-    CUDA_TRY(c, cudaEventRecord(c->pin_free, st));
+    CUDA_TRY(c, staged(c, st));
     return MT4G_OK;
 }
 
@@ -783,6 +1025,7 @@ extern "C" {
 int mt4g_cnn_init(mt4g_ctx *c, uint64_t seed) {
     int rc = begin_call(c);
     if (rc) return rc;
+    c->cnn_version++;
     rc = ensure_cnn_state(c);
     if (rc) return rc;
     std::vector<float> w;
@@ -808,6 +1051,7 @@ int mt4g_cnn_get_params(mt4g_ctx *c, float *host_out) {
 int mt4g_cnn_set_params(mt4g_ctx *c, const float *host_in) {
     int rc = begin_call(c);
     if (rc) return rc;
+    c->cnn_version++;
     if (!host_in) return fail(c, MT4G_EINVAL, "NULL input");
     rc = ensure_cnn_state(c);
     if (rc) return rc;
@@ -844,6 +1088,7 @@ int mt4g_cnn_save(mt4g_ctx *c, const char *path) {
 int mt4g_cnn_load(mt4g_ctx *c, const char *path) {
     int rc = begin_call(c);
     if (rc) return rc;
+    c->cnn_version++;
     if (!path) return fail(c, MT4G_EINVAL, "NULL path");
     FILE *f = fopen(path, "rb");
     if (!f) return fail(c, MT4G_EINVAL, "cannot open %s", path);
@@ -965,6 +1210,7 @@ int mt4g_cnn_train_step(mt4g_ctx *c, const uint16_t *feat, int32_t T, int64_t B,
     cudaStream_t st = (cudaStream_t)cuda_stream;
     rc = cnn_fwd_bwd(c, feat, T, B, cp_count, cp_idx, max_cp, c->cnn.grad, loss_out, st);
     if (rc) return rc;
+    c->cnn_version++;
     CUDA_TRY(c, cnn_adam(c->cnn, c->cnn.grad, lr, st));
     return MT4G_OK;
 }
@@ -1012,6 +1258,11 @@ int mt4g_propose(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets,
 
 namespace {
 
+int presize_cnn(mt4g_ctx *ctx, int64_t rows, int64_t S) {
+    CnnBuffers C;
+    return ensure_cnn_ws(ctx, carve_cnn(nullptr, rows, S, false, true, ctx->n_win, C));
+}
+
 // Learned mode: features, logits and windows of every series (after the sort has written
 // the medians), for the learned init kernel and the probe groups.
 int enqueue_proposals(mt4g_ctx *ctx, const uint32_t *samples, Plan &P, Buffers &B, RunParams &R, cudaStream_t st) {
@@ -1046,4 +1297,183 @@ extern "C" int mt4g_learned_stats(mt4g_ctx *c, int64_t *out) {
     out[1] = (int64_t)c->h_hdr->refined;
     out[2] = (int64_t)c->h_hdr->rec_next;
     return MT4G_OK;
+}
+
+
+extern "C" int mt4g_selftest_wait_timeout(mt4g_ctx *ctx, int64_t limit_ns, void *cuda_stream) {
+    int rc = begin_call(ctx);
+    if (rc) return rc;
+    if (limit_ns <= 0 || limit_ns > 2000000000LL) return fail(ctx, MT4G_EINVAL, "limit must be in (0, 2e9] ns");
+    // a one-series plan only to size the workspace; the queue header then claims one pending
+    // item that is never published, so every warp's bounded wait expires
+    const int64_t offsets[2] = {0, 2};
+    const int32_t steps[1] = {2};
+    Plan P;
+    rc = make_plan(ctx, offsets, steps, 1, MT4G_MODE_FULL, 1, P);
+    if (rc) return rc;
+    size_t ready_off = 0;
+    Buffers B;
+    const size_t need = carve(nullptr, P, B, &ready_off);
+    rc = ensure_workspace(ctx, need);
+    if (rc) return rc;
+    carve(ctx->ws, P, B, &ready_off);
+    ctx->ready_off = (size_t)-1;  // the flags are cleared below; force a clear on the next call too
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    rc = ensure_pinned(ctx, sizeof(QueueHeader));
+    if (rc) return rc;
+    QueueHeader hq{};
+    hq.pending = 1;
+    hq.tail = 0;
+    hq.cap = P.cap;
+    memcpy(ctx->pin, &hq, sizeof(hq));
+    CUDA_TRY(ctx, cudaMemcpyAsync(B.q, ctx->pin, sizeof(hq), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(ctx, cudaEventRecord(ctx->pin_free, st));
+    CUDA_TRY(ctx, cudaMemsetAsync(B.ready, 0, P.cap * sizeof(int32_t), st));
+    RunParams R{};
+    R.desc = B.desc;
+    R.lab = B.labA;
+    R.runs = B.runs;
+    R.q = B.q;
+    R.items = B.items;
+    R.ready = B.ready;
+    R.gcount = B.gcount;
+    R.mode = kRunScan;
+    R.min_seg = 1;
+    R.wait_limit_ns = limit_ns;
+    CUDA_TRY(ctx, launch_queue_run(R, ctx->grid, 1u << 16, st));
+    return finish_call(ctx, B, st);
+}
+
+extern "C" double mt4g_critical_value(double alpha, int64_t n_left, int64_t n_right) {
+    if (!(alpha > 0.0 && alpha < 1.0) || n_left < 1 || n_right < 1) return -1.0;
+    return sqrt(-0.5 * log(alpha / 2.0) * (double)(n_left + n_right) / ((double)n_left * (double)n_right));
+}
+
+
+extern "C" int mt4g_autotune(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets, const int32_t *steps,
+                             int64_t S, void *cuda_stream) {
+    int rc = begin_call(ctx);
+    if (rc) return rc;
+    Plan P;
+    rc = make_plan(ctx, offsets, steps, S, MT4G_MODE_FULL, 1, P);
+    if (rc) return rc;
+    if (S == 0) return MT4G_OK;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    std::map<std::pair<int, int>, std::vector<int64_t>> buckets;
+    for (int64_t s = 0; s < S; s++) {
+        auto &v = buckets[{ilog2(P.desc[s].T), ilog2(P.desc[s].m)}];
+        if (v.size() < 256) v.push_back(s);
+    }
+    const bool was_graph = ctx->use_graph, was_timing = ctx->timing;
+    const int32_t was_forced = ctx->forced_kpt;
+    ctx->use_graph = false;
+    ctx->timing = false;
+    uint32_t *gather = nullptr;
+    int32_t *ko = nullptr;
+    int64_t *no = nullptr, *dn = nullptr;
+    double *po = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    rc = MT4G_OK;
+    for (auto &kv : buckets) {
+        const std::vector<int64_t> &ids = kv.second;
+        const int64_t n = (int64_t)ids.size();
+        std::vector<int64_t> offs(n + 1, 0);
+        std::vector<int32_t> stp(n);
+        for (int64_t i = 0; i < n; i++) {
+            stp[i] = steps[ids[i]];
+            offs[i + 1] = offs[i] + (offsets[ids[i] + 1] - offsets[ids[i]]);
+        }
+        if (!gather) {
+            // one buffer big enough for the largest bucket sample (at most 256 series)
+            int64_t mx = 0;
+            for (auto &kv2 : buckets) {
+                int64_t t = 0;
+                for (int64_t id : kv2.second) t += offsets[id + 1] - offsets[id];
+                mx = std::max(mx, t);
+            }
+            if (cudaMalloc(&gather, (size_t)mx * 4) != cudaSuccess || cudaMalloc(&ko, 256 * 4) != cudaSuccess ||
+                cudaMalloc(&no, 256 * 8) != cudaSuccess || cudaMalloc(&dn, 256 * 8) != cudaSuccess ||
+                cudaMalloc(&po, 256 * 8) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+                cudaEventCreate(&e1) != cudaSuccess) {
+                rc = fail(ctx, MT4G_ENOMEM, "autotune buffers");
+                break;
+            }
+        }
+        for (int64_t i = 0; i < n; i++)
+            if (cudaMemcpyAsync(gather + offs[i], samples + offsets[ids[i]], (size_t)(offs[i + 1] - offs[i]) * 4,
+                                cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+                rc = fail(ctx, MT4G_ECUDA, "autotune gather");
+                break;
+            }
+        if (rc) break;
+        float best_ms = 1e30f;
+        int32_t best = 1;
+        for (int32_t kpt : {1, 2, 4}) {
+            ctx->forced_kpt = kpt;
+            float ms = 0.f;
+            for (int rep = 0; rep < 3 && !rc; rep++) {  // first call warms up, the minimum of the rest counts
+                cudaEventRecord(e0, st);
+                rc = scan_body(ctx, gather, offs.data(), stp.data(), n, MT4G_MODE_FULL, ko, no, dn, po, st);
+                cudaEventRecord(e1, st);
+                if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = fail(ctx, MT4G_ECUDA, "autotune timing");
+                float t = 0.f;
+                cudaEventElapsedTime(&t, e0, e1);
+                if (rep == 1 || (rep > 1 && t < ms)) ms = t;
+            }
+            if (rc) break;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = kpt;
+            }
+        }
+        if (rc) break;
+        ctx->tune[kv.first] = best;
+    }
+    ctx->forced_kpt = was_forced;
+    ctx->use_graph = was_graph;
+    ctx->timing = was_timing;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(gather);
+    cudaFree(ko);
+    cudaFree(no);
+    cudaFree(dn);
+    cudaFree(po);
+    return rc;
+}
+
+extern "C" int mt4g_autotune_save(mt4g_ctx *ctx, const char *path) {
+    if (!ctx || !path) return MT4G_EINVAL;
+    FILE *f = fopen(path, "w");
+    if (!f) return fail(ctx, MT4G_EINVAL, "cannot open %s", path);
+    fprintf(f, "# log2(T) log2(m) scan-tile\n");
+    for (auto &kv : ctx->tune) fprintf(f, "%d %d %d\n", kv.first.first, kv.first.second, kv.second);
+    fclose(f);
+    return MT4G_OK;
+}
+
+extern "C" int mt4g_autotune_load(mt4g_ctx *ctx, const char *path) {
+    if (!ctx || !path) return MT4G_EINVAL;
+    FILE *f = fopen(path, "r");
+    if (!f) return fail(ctx, MT4G_EINVAL, "cannot open %s", path);
+    std::map<std::pair<int, int>, int32_t> t;
+    char line[256];
+    while (fgets(line, sizeof(line), f)) {
+        if (line[0] == '#') continue;
+        int a = 0, b = 0, k = 0;
+        if (sscanf(line, "%d %d %d", &a, &b, &k) != 3 || (k != 1 && k != 2 && k != 4)) {
+            fclose(f);
+            return fail(ctx, MT4G_EINVAL, "%s: bad line", path);
+        }
+        t[{a, b}] = k;
+    }
+    fclose(f);
+    ctx->tune = t;
+    return MT4G_OK;
+}
+
+extern "C" int mt4g_autotune_get(mt4g_ctx *ctx, int32_t T, int32_t m) {
+    if (!ctx || T < 1 || m < 1) return MT4G_EINVAL;
+    return pick_kpt(ctx, T, m);
 }

@@ -35,3 +35,12 @@ def test_no_cpu_fallback_without_device():
         pytest.skip("a GPU is present")
     with pytest.raises(Exception):
         mt4g.Engine(0)
+
+
+def test_critical_value_matches_oracle():
+    """Eq. 1 as computed by the library (host code) against the oracle's reading of it."""
+    import oracle
+    for alpha in (0.1, 0.05, 1e-3, 1e-6):
+        for n, m in ((10, 20), (128, 384), (65536, 4096)):
+            assert abs(mt4g.critical_value(alpha, n, m) - oracle.critical_value(alpha, n, m)) < 1e-15
+    assert mt4g.critical_value(1.5, 3, 3) == -1.0 and mt4g.critical_value(0.05, 0, 3) == -1.0

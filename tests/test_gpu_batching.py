@@ -1,0 +1,98 @@
+"""Batching machinery on the GPU: CUDA-graph replay and the scan-tile autotuner.
+
+Neither changes any result: graph replays and tuned tiles must give exactly the answers of direct
+calls with the default tile (which are checked against the oracle elsewhere).
+"""
+import numpy as np
+import pytest
+
+import paper_2511_05958_b300 as mt4g
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture()
+def eng():
+    import torch
+    assert torch.cuda.is_available()
+    e = mt4g.Engine(0)
+    yield e
+    e.close()
+
+
+def _seg(eng, d, b, mode=mt4g.MODE_FULL, out=None):
+    r = eng.ks_segment(d, b.offsets, b.steps, 1e-6, 1, 16, mode=mode, out=out)
+    return r, [t.cpu().numpy().copy() for t in r[1:6]]
+
+
+def _same(x, y):
+    for a, c in zip(x, y):
+        assert np.array_equal(a, c)
+
+
+def test_graph_replay_matches_direct_calls(eng):
+    b = synth.generate(2, 41, 64)
+    d = mt4g.to_device_samples(b.samples)
+    _, ref = _seg(eng, d, b)
+    eng.set_option(mt4g.OPT_GRAPH, 1)
+    r1, g1 = _seg(eng, d, b)          # captured
+    _same(ref, g1)
+    r2, g2 = _seg(eng, d, b, out=r1)  # replayed (same pointers and tables)
+    _same(ref, g2)
+    # new data behind the same pointer: the replay reads it
+    b2 = synth.generate(2, 42, 64)
+    d.copy_(mt4g.to_device_samples(b2.samples))
+    _, g3 = _seg(eng, d, b2, out=r1)
+    eng.set_option(mt4g.OPT_GRAPH, 0)
+    _, ref3 = _seg(eng, d, b2)
+    _same(ref3, g3)
+    # a different shape is captured again
+    eng.set_option(mt4g.OPT_GRAPH, 1)
+    b3 = synth.generate(3, 2, 40)
+    d3 = mt4g.to_device_samples(b3.samples)
+    _, g4 = _seg(eng, d3, b3)
+    eng.set_option(mt4g.OPT_GRAPH, 0)
+    _, ref4 = _seg(eng, d3, b3)
+    _same(ref4, g4)
+
+
+def test_graph_replay_scan_and_learned(eng):
+    b = synth.generate(2, 43, 48)
+    d = mt4g.to_device_samples(b.samples)
+    ref_scan = [t.cpu().numpy() for t in eng.ks_scan(d, b.offsets, b.steps)]
+    eng.cnn_init(4)
+    eng.set_option(mt4g.OPT_CONF_MIN_PPM, 0)
+    _, ref_l = _seg(eng, d, b, mode=mt4g.MODE_LEARNED)
+    eng.set_option(mt4g.OPT_GRAPH, 1)
+    out = eng.ks_scan(d, b.offsets, b.steps)
+    for _ in range(2):
+        out = eng.ks_scan(d, b.offsets, b.steps, out=out)
+        for a, c in zip(ref_scan, out):
+            assert np.array_equal(a, c.cpu().numpy())
+    r, g1 = _seg(eng, d, b, mode=mt4g.MODE_LEARNED)
+    _, g2 = _seg(eng, d, b, mode=mt4g.MODE_LEARNED, out=r)
+    _same(ref_l, g1)
+    _same(ref_l, g2)
+    eng.set_option(mt4g.OPT_GRAPH, 0)
+    eng.set_option(mt4g.OPT_CONF_MIN_PPM, 900000)
+
+
+def test_autotune_keeps_results_and_roundtrips(eng, tmp_path):
+    b = synth.generate(3, 2, 300)
+    keep = [s for s in range(300) if float(b.steps[s]) ** 2 * float(b.m[s]) < 3e8][:120]
+    bb = synth.from_arrays([b.series(s) for s in keep])
+    d = mt4g.to_device_samples(bb.samples)
+    _, ref = _seg(eng, d, bb)
+    eng.autotune(d, bb.offsets, bb.steps)
+    tiles = {eng.autotune_get(int(T), int(m)) for T, m in zip(bb.steps, bb.m)}
+    assert tiles <= {1, 2, 4}
+    _, tuned = _seg(eng, d, bb)
+    _same(ref, tuned)
+    path = str(tmp_path / "tune.txt")
+    eng.autotune_save(path)
+    e2 = mt4g.Engine(0)
+    e2.autotune_load(path)
+    for T, m in zip(bb.steps, bb.m):
+        assert e2.autotune_get(int(T), int(m)) == eng.autotune_get(int(T), int(m))
+    e2.close()

@@ -268,3 +268,12 @@ def test_config3_uneven_batch_sampled(eng):
     assert np.array_equal(den[sample], oden)
     assert_p_close(p[sample], op)
     assert (num <= den).all() and (num >= 0).all()
+
+
+def test_bounded_wait_expires_and_context_survives(eng):
+    """A queue claiming work that never arrives: the bounded waits end with ETIMEOUT (no hang,
+    no fault), and the next ordinary call on the same context is correct."""
+    assert eng.selftest_wait_timeout(20_000_000) == mt4g.ETIMEOUT
+    b = synth.generate(1, 0, 1)
+    check_scan(eng, b)
+    check_segment(eng, b, 1e-6)
