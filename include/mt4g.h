@@ -225,6 +225,20 @@ int mt4g_autotune_get(mt4g_ctx *ctx, int32_t T, int32_t m);
  * Returns -1 for alpha outside (0, 1) or a sample size below 1.  Host function. */
 double mt4g_critical_value(double alpha, int64_t n_left, int64_t n_right);
 
+/* Load-latency statistics of every series (paper Sec. IV-C: MT4G reports the average as the
+ * main result, with p50, p95 and the standard deviation), over all T_s * m_s samples of a
+ * series; samples and host tables as for mt4g_ks_scan.  Definitions (the paper names the
+ * statistics, not their estimators):
+ *   mean_out[s] = (sum x) / N, the exact integer sum rounded once to FP64;
+ *   p50_out[s], p95_out[s] = sorted[ceil(q N) - 1] for q = 1/2 and 95/100 (nearest rank);
+ *   std_out[s] = sqrt((N sum x^2 - (sum x)^2) / N^2), the population standard deviation with
+ *   an exact 128-bit numerator rounded once to FP64 (nearest, ties to even).
+ * Outputs: DEVICE double [S], uint32 [S], uint32 [S], double [S].  The order statistics come
+ * from the same per-series sort the scan uses; the sums from one more read of the samples. */
+int mt4g_latency_stats(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets, const int32_t *steps,
+                       int64_t S, double *mean_out, uint32_t *p50_out, uint32_t *p95_out, double *std_out,
+                       void *cuda_stream);
+
 /*
  * Allocation-free variant of mt4g_ks_scan (no counterpart in the paper).
  *
@@ -265,6 +279,12 @@ int mt4g_ks_scan_noalloc(const uint32_t *samples, const int64_t *offsets, const 
  */
 int mt4g_stage_times(mt4g_ctx *ctx, double *ms_out, int32_t max_calls);
 int mt4g_last_work(mt4g_ctx *ctx, int64_t *evals);
+/* mt4g_int32_peak: the measured ceiling of the scan's inner step.  Runs the step's integer
+ * mix (two multiply-adds, an absolute value, a max: 4 ops per (split, distinct value)
+ * evaluation) with independent chains on every SM of CUDA device `device` for a few ms, and
+ * writes the best of three timed launches in 10^12 integer ops/s to *tops_out (host).
+ * Synchronous; uses its own stream; allocates nothing.  MT4G_OK or MT4G_ECUDA. */
+int mt4g_int32_peak(int device, double *tops_out);
 /* Failure-detection self-test (no counterpart in the paper): runs the work-queue kernel
  * over a queue that claims one pending item and never publishes it, with every wait bounded
  * by limit_ns (<= 2e9).  mt4g_wait() must then return MT4G_ETIMEOUT, and the context stays

@@ -10,6 +10,7 @@ in its docstring; the C file's header states the readings taken where the paper 
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 
@@ -153,3 +154,35 @@ def ks_segment(samples, offsets, steps, alpha: float, min_seg: int = 1, max_cp: 
     if rc not in (OK, ECAPACITY):
         raise ValueError(f"oracle_ks_segment rc={rc}")
     return rc, cnt, idx, num, den, p
+
+
+def latency_stats(samples, offsets, steps):
+    """Load-latency statistics of each series (Sec. IV-C: the average as the main result, plus
+    p50, p95 and the standard deviation), over all T*m samples of the series.
+
+    Readings (the paper names the statistics but not their estimators):
+      mean = (sum x) / N, the exact integer sum rounded once to FP64, then one FP64 division;
+      p50, p95 = nearest-rank order statistics, sorted[ceil(q N) - 1] with ceil(q N) taken
+          exactly (q = 50/100 and 95/100);
+      std = sqrt(var), var = (N sum x^2 - (sum x)^2) / N^2 (population variance): the exact
+          integer numerator rounded once to FP64, divided by the FP64 product N * N.
+    Returns (mean, p50, p95, std) arrays of length S.
+    """
+    samples = np.asarray(samples, dtype=np.uint32)
+    offsets = np.asarray(offsets, dtype=np.int64)
+    S = len(offsets) - 1
+    mean = np.empty(S, np.float64)
+    std = np.empty(S, np.float64)
+    p50 = np.empty(S, np.uint32)
+    p95 = np.empty(S, np.uint32)
+    for s in range(S):
+        x = samples[offsets[s]:offsets[s + 1]]
+        N = int(x.size)
+        sx = int(x.astype(np.uint64).sum())
+        sxx = sum(int(v) * int(v) for v in x.tolist())
+        mean[s] = float(sx) / float(N)
+        std[s] = math.sqrt(float(N * sxx - sx * sx) / (float(N) * float(N)))
+        xs = np.sort(x)
+        p50[s] = xs[(50 * N + 99) // 100 - 1]
+        p95[s] = xs[(95 * N + 99) // 100 - 1]
+    return mean, p50, p95, std

@@ -72,6 +72,8 @@ def load_library():
     L.mt4g_critical_value.argtypes = [dbl, i64, i64]
     L.mt4g_critical_value.restype = dbl
     L.mt4g_stage_times.argtypes = [vp, vp, i32]
+    L.mt4g_int32_peak.argtypes = [ctypes.c_int, vp]
+    L.mt4g_latency_stats.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp, vp, vp]
     L.mt4g_last_work.argtypes = [vp, vp]
     L.mt4g_summaries.argtypes = [vp, vp, vp, vp, i64, vp, vp]
     L.mt4g_cnn_init.argtypes = [vp, ctypes.c_uint64]
@@ -94,7 +96,8 @@ def exported_symbols():
             "mt4g_summaries", "mt4g_cnn_init", "mt4g_cnn_get_params", "mt4g_cnn_set_params", "mt4g_cnn_save",
             "mt4g_cnn_load", "mt4g_cnn_forward", "mt4g_cnn_grads", "mt4g_cnn_train_step", "mt4g_propose",
             "mt4g_learned_stats", "mt4g_ks_scan_noalloc", "mt4g_selftest_wait_timeout", "mt4g_critical_value",
-            "mt4g_autotune", "mt4g_autotune_save", "mt4g_autotune_load", "mt4g_autotune_get"]
+            "mt4g_autotune", "mt4g_autotune_save", "mt4g_autotune_load", "mt4g_autotune_get",
+            "mt4g_int32_peak", "mt4g_latency_stats"]
 
 
 class ScanResult(NamedTuple):
@@ -267,6 +270,15 @@ class Engine:
         return out._replace(rc=status)
 
 
+def int32_peak(device: int = 0) -> float:
+    """Measured rate (10^12 ops/s) of the scan's integer step mix on every SM (mt4g_int32_peak)."""
+    v = np.zeros(1, np.float64)
+    rc = load_library().mt4g_int32_peak(int(device), v.ctypes.data_as(ctypes.c_void_p))
+    if rc != OK:
+        raise Mt4gError(rc, "mt4g_int32_peak failed")
+    return float(v[0])
+
+
 def critical_value(alpha: float, n_left: int, n_right: int) -> float:
     """Eq. 1 critical value of D (host computation in the library)."""
     return float(load_library().mt4g_critical_value(float(alpha), int(n_left), int(n_right)))
@@ -294,6 +306,25 @@ def _mixin_learned(cls):
         if sync:
             self._check(self.wait())
         return out
+
+    def latency_stats(self, samples, offsets, steps, stream=None, sync=True):
+        """mt4g_latency_stats: per-series (mean, p50, p95, std) device tensors."""
+        import torch
+        offsets, steps = _host_tables(offsets, steps)
+        S = steps.shape[0]
+        dev = samples.device
+        mean = torch.empty(S, dtype=torch.float64, device=dev)
+        std = torch.empty(S, dtype=torch.float64, device=dev)
+        p50 = torch.empty(S, dtype=torch.int32, device=dev)
+        p95 = torch.empty(S, dtype=torch.int32, device=dev)
+        self._check(self._L.mt4g_latency_stats(self._h, _dev_ptr(samples, "samples"),
+                                               offsets.ctypes.data_as(ctypes.c_void_p),
+                                               steps.ctypes.data_as(ctypes.c_void_p), S, _dev_ptr(mean, "mean"),
+                                               _dev_ptr(p50, "p50"), _dev_ptr(p95, "p95"), _dev_ptr(std, "std"),
+                                               _stream_handle(stream)))
+        if sync:
+            self._check(self.wait())
+        return mean, p50, p95, std
 
     def cnn_init(self, seed: int):
         self._check(self._L.mt4g_cnn_init(self._h, int(seed)))

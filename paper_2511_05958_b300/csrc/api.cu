@@ -1135,6 +1135,29 @@ int mt4g_summaries(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offset
     return finish_call(ctx, B, st);
 }
 
+int mt4g_latency_stats(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets, const int32_t *steps,
+                       int64_t S, double *mean_out, uint32_t *p50_out, uint32_t *p95_out, double *std_out,
+                       void *cuda_stream) {
+    int rc = begin_call(ctx);
+    if (rc) return rc;
+    if (S > 0 && (!samples || !mean_out || !p50_out || !p95_out || !std_out))
+        return fail(ctx, MT4G_EINVAL, "NULL device pointer");
+    Plan P;
+    rc = make_plan(ctx, offsets, steps, S, MT4G_MODE_FULL, 1, P);
+    if (rc) return rc;
+    if (S == 0) return MT4G_OK;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    Buffers B;
+    RunParams R;
+    mark(ctx, 0, st);
+    const int epoch = enqueue_pipeline(ctx, samples, P, R, B, st);
+    if (epoch < 0) return epoch;
+    mark(ctx, 3, st);
+    CUDA_TRY(ctx, launch_latency_stats(samples, B.desc, S, mean_out, p50_out, p95_out, std_out, st));
+    mark(ctx, 4, st);
+    return finish_call(ctx, B, st);
+}
+
 int mt4g_cnn_forward(mt4g_ctx *c, const uint16_t *feat, const int32_t *steps, int64_t S, float *logits_out,
                      void *cuda_stream) {
     int rc = begin_call(c);

@@ -33,6 +33,8 @@ struct SeriesDesc {
     int32_t nruns;      // U_s, number of distinct values (written by the sort)
     int32_t kpt;        // split groups of 32 per warp work item (1, 2 or 4): the scan tile
     uint32_t median;    // sorted value at index N / 2 (written by the sort)
+    uint32_t p50;       // nearest-rank order statistics sorted[ceil(q N) - 1], q = 1/2 and
+    uint32_t p95;       // 95/100 (written by the sort)
     int32_t pad;
 };
 
@@ -157,6 +159,8 @@ cudaError_t launch_collect(const SeriesDesc *desc, int64_t S, const uint8_t *cp_
 cudaError_t launch_summaries(const uint32_t *samples, const SeriesDesc *raw_desc, int64_t S, uint16_t *feat,
                              cudaStream_t st);
 
+cudaError_t launch_latency_stats(const uint32_t *samples, const SeriesDesc *desc, int64_t S, double *mean_out,
+                                 uint32_t *p50_out, uint32_t *p95_out, double *std_out, cudaStream_t st);
 cudaError_t launch_reduce_rank(const uint32_t *samples, const SeriesDesc *raw_desc, int64_t S,
                                double *red, uint32_t *rank_out, cudaStream_t st);
 

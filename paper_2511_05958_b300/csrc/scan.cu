@@ -30,6 +30,7 @@
 // counts itself done in the group's counter; the last member combines the group,
 // computes p and, if p <= alpha, records the change point and pushes the children.
 #include <climits>
+#include <type_traits>
 
 #include "mt4g_internal.cuh"
 
@@ -158,8 +159,9 @@ union StageUnion {
 // 32-bin histogram for counting differentiating samples.
 struct WarpStage {
     StageUnion u;
-    int4 run[32];
-    uint4 lbl[32];  // up to 8 differentiating labels of each staged run (16-bit each)
+    int2 pre[32];   // inclusive prefix over the staged runs of (labels below k0, in-segment samples)
+    int4 meta[32];  // per staged run with differentiating labels: (first such position, L | flags, M1, M2)
+    uint4 lbl[32];  // up to 8 labels from that position (16-bit each), for runs with repeats
     int hist[32];
 };
 
@@ -182,22 +184,41 @@ __device__ __forceinline__ int count_below(const uint16_t *__restrict__ lab, int
 // [k0 + 32 q, k0 + 32 q + 32) distinguish the lanes, and each lane counts those below its
 // own k, by broadcast for up to kShflMax of them, else by a search in that short sorted
 // slice.  Empty runs are compacted away; the walk visits the runs in value order.
-// One-group (32-split) slice with int4 staging and histogram counting (the common tile).
+//
+// One-group (32-split) slice, the common tile.  Staging (lane = run) also forms, over the
+// batch, inclusive prefix sums of the labels below k0 and of the in-segment samples, so that
+// at run r of the batch
+//     H c_L - a C = K + H cbs_r - a ns_r,
+// with K carried from the previous batches plus H times this lane's differentiating labels
+// met so far.  A run without differentiating labels (most runs) then costs one shared load
+// and the two multiply-adds, |.| and max of the definition.  For the others the lane's count
+// comes from bit masks of the window offsets (first and second occurrences: two AND + POPC)
+// when at most kShflMax labels fall in the window and none repeats more than twice, else from
+// the staged labels, a 32-bin histogram, or a search.  The first kShflMax labels from the
+// window start are loaded together during staging; they also give the window's end without a
+// second search unless more than kShflMax labels fall in it.
 template <bool WIDE>
 __device__ void scan_slice1(const uint16_t *__restrict__ lab, const int32_t *__restrict__ rt, int U, int T, int lo,
                             int hi, int k0, WarpStage &ws, uint64_t &g_out, int &nonempty) {
+    using Acc = typename std::conditional<WIDE, int64_t, uint32_t>::type;
     const int lane = threadIdx.x & 31;
     const int k = k0 + lane, k1 = k0 + 32;
-    const uint32_t H = (uint32_t)(hi - lo);
-    const uint32_t a = (uint32_t)(k - lo);
-    uint32_t cl = 0, C = 0, mx32 = 0;
+    const unsigned lt = lanemask_lt();
+    const Acc H = (Acc)(hi - lo);
+    const Acc a = (Acc)(k - lo);
+    // K = H c_L - a C over the runs walked so far (c_L counts labels below this lane's k); the
+    // value at a run of the current batch is K + H (labels below k0 up to it) - a (samples up to it)
+    // plus H times the lane's differentiating labels met so far.
+    Acc K = 0;
+    uint32_t mx32 = 0;
     uint64_t mx = 0;
     nonempty = 0;
     ws.hist[lane] = 0;
     __syncwarp();
     for (int j0 = 0; j0 < U; j0 += 32) {
         const int j = j0 + lane;
-        int si = 0, ei = 0, cb = 0, ce = 0;
+        int si = 0, ei = 0, c0 = 0, n_av = 0, L = 0;
+        bool la_lt = false;
         if (j < U) {
             const int a0 = __ldg(rt + j), b0 = __ldg(rt + j + 1);
             const int f0 = __ldg(lab + a0), l0 = __ldg(lab + b0 - 1);
@@ -206,75 +227,128 @@ __device__ void scan_slice1(const uint16_t *__restrict__ lab, const int32_t *__r
             if (ei > si) {
                 const int fi = (si == a0) ? f0 : __ldg(lab + si);
                 const int la = (ei == b0) ? l0 : __ldg(lab + ei - 1);
-                const int c0 = count_below(lab, si, ei, fi, la, si, k0);
-                cb = c0 - si;
-                ce = count_below(lab, si, ei, fi, la, c0, k1) - si;
+                c0 = count_below(lab, si, ei, fi, la, si, k0);
+                n_av = min(kShflMax, ei - c0);
+                la_lt = la < k1;
             }
         }
-        // prefetch the few labels that distinguish the lanes (independent loads across lanes)
+        // The labels from c0 on are sorted: load up to kShflMax of them at once.  Those below k1
+        // distinguish the lanes; the rest lie above every split of the slice.
         uint32_t pk[4] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu};
-        const int Lr = ce - cb;
-        if (Lr > 0 && Lr <= kShflMax) {
-            const uint16_t *src = lab + si + cb;
+        uint32_t M1 = 0, M2 = 0;
+        bool multi = false;
+        int below = 0;
+        if (n_av > 0) {
+            const uint16_t *src = lab + c0;
 #pragma unroll
             for (int q = 0; q < kShflMax; q++) {
-                const uint32_t v = q < Lr ? (uint32_t)__ldg(src + q) : 0xffffu;
+                const uint32_t v = q < n_av ? (uint32_t)__ldg(src + q) : 0xffffu;
                 pk[q >> 1] = (q & 1) ? ((pk[q >> 1] & 0xffffu) | (v << 16)) : ((pk[q >> 1] & 0xffff0000u) | v);
+                if (v < (uint32_t)k1) {
+                    // offsets from k0 as bits: first occurrences in M1, second in M2
+                    const uint32_t bit = 1u << (v - (uint32_t)k0);
+                    below++;
+                    multi |= (M2 & bit) != 0;
+                    M2 |= M1 & bit;
+                    M1 |= bit;
+                }
+            }
+        }
+        if (ei > si) {
+            if (la_lt)
+                L = ei - c0;
+            else if (below < n_av || n_av == ei - c0)
+                L = below;
+            else
+                L = lower_bound_lab(lab, c0 + n_av, ei, k1) - c0;
+        }
+        // inclusive prefix sums over the batch of the labels below k0 and of the samples
+        int cbs = ei > si ? c0 - si : 0, ns = ei - si;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y1 = __shfl_up_sync(kFull, cbs, o), y2 = __shfl_up_sync(kFull, ns, o);
+            if (lane >= o) {
+                cbs += y1;
+                ns += y2;
             }
         }
         const unsigned ne = __ballot_sync(kFull, ei > si);
+        const int pos = __popc(ne & lt);
+        unsigned spec = 0;  // staged positions of runs with differentiating labels
         if (ei > si) {
-            const int pos = __popc(ne & lanemask_lt());
-            ws.run[pos] = make_int4(si, ei, cb, ce);
-            ws.lbl[pos] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            ws.pre[pos] = make_int2(cbs, ns);
+            if (L > 0) {
+                spec = 1u << pos;
+                ws.meta[pos] = make_int4(c0, L | ((L > kShflMax || multi) ? 0x10000 : 0), (int)M1, (int)M2);
+                if (multi) ws.lbl[pos] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            }
         }
+        spec = __reduce_or_sync(kFull, spec);
+        const int cbt = __shfl_sync(kFull, cbs, 31), nt = __shfl_sync(kFull, ns, 31);
         __syncwarp();
         const int cnt = __popc(ne);
-        for (int r = 0; r < cnt; r++) {
-            const int4 q = ws.run[r];
-            C += (uint32_t)(q.y - q.x);
-            uint32_t add = (uint32_t)q.z;
-            const int L = q.w - q.z;
-            if (L > 0) {  // warp-uniform
-                const int sb = q.x + q.z;
-                if (L <= kShflMax) {
-                    // staged labels; unused slots hold 0xffff, above every k
-                    const uint4 lb4 = ws.lbl[r];
-                    const uint32_t w4[4] = {lb4.x, lb4.y, lb4.z, lb4.w};
-#pragma unroll
-                    for (int t = 0; t < 4; t++)
-                        add += (uint32_t)((int)(w4[t] & 0xffffu) < k) + (uint32_t)((int)(w4[t] >> 16) < k);
-                } else if (L <= 32) {
-                    // histogram of the slice's labels over the 32 lanes, then an exclusive scan
-                    const int bin = lane < L ? (int)__ldg(lab + sb + lane) - k0 : -1;
-                    if (bin >= 0) atomicAdd(&ws.hist[bin], 1);
-                    __syncwarp();
-                    const int hv = ws.hist[lane];
-                    int incl = hv;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int y = __shfl_up_sync(kFull, incl, o);
-                        if (lane >= o) incl += y;
-                    }
-                    add += (uint32_t)(incl - hv);
-                    __syncwarp();
-                    if (bin >= 0) ws.hist[bin] = 0;
-                    __syncwarp();
+        int r = 0;
+        for (;;) {
+            const int nxt = spec ? __ffs(spec) - 1 : cnt;
+#pragma unroll 4
+            for (; r < nxt; r++) {
+                const int2 p = ws.pre[r];
+                if (WIDE) {
+                    const int64_t f = K + H * (int64_t)p.x - a * (int64_t)p.y;
+                    const uint64_t af = (uint64_t)(f < 0 ? -f : f);
+                    mx = af > mx ? af : mx;
                 } else {
-                    add += (uint32_t)(lower_bound_lab(lab, sb, sb + L, k) - sb);
+                    const int32_t f = (int32_t)(K + H * (uint32_t)p.x - a * (uint32_t)p.y);
+                    mx32 = max(mx32, (uint32_t)(f < 0 ? -f : f));
                 }
             }
-            cl += add;
+            if (nxt >= cnt) break;
+            // a run with differentiating labels: this lane's count of them below its k
+            const int4 mt = ws.meta[nxt];
+            const int Lr = mt.y & 0xffff;
+            uint32_t add;
+            if (!(mt.y >> 16)) {
+                add = (uint32_t)(__popc((unsigned)mt.z & lt) + __popc((unsigned)mt.w & lt));
+            } else if (Lr <= kShflMax) {
+                const uint4 lb4 = ws.lbl[nxt];
+                const uint32_t w4[4] = {lb4.x, lb4.y, lb4.z, lb4.w};
+                add = 0;
+#pragma unroll
+                for (int t = 0; t < 4; t++)
+                    add += (uint32_t)((int)(w4[t] & 0xffffu) < k) + (uint32_t)((int)(w4[t] >> 16) < k);
+            } else if (Lr <= 32) {
+                // histogram of the slice's labels over the 32 lanes, then an exclusive scan
+                const int bin = lane < Lr ? (int)__ldg(lab + mt.x + lane) - k0 : -1;
+                if (bin >= 0) atomicAdd(&ws.hist[bin], 1);
+                __syncwarp();
+                const int hv = ws.hist[lane];
+                int incl = hv;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(kFull, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                add = (uint32_t)(incl - hv);
+                __syncwarp();
+                if (bin >= 0) ws.hist[bin] = 0;
+                __syncwarp();
+            } else {
+                add = (uint32_t)(lower_bound_lab(lab, mt.x, mt.x + Lr, k) - mt.x);
+            }
+            K += H * (Acc)add;
+            const int2 p = ws.pre[nxt];
             if (WIDE) {
-                const int64_t f = (int64_t)H * cl - (int64_t)a * C;
+                const int64_t f = K + H * (int64_t)p.x - a * (int64_t)p.y;
                 const uint64_t af = (uint64_t)(f < 0 ? -f : f);
                 mx = af > mx ? af : mx;
             } else {
-                const int32_t f = (int32_t)(H * cl - a * C);
-                const uint32_t af = (uint32_t)(f < 0 ? -f : f);
-                mx32 = max(mx32, af);
+                const int32_t f = (int32_t)(K + H * (uint32_t)p.x - a * (uint32_t)p.y);
+                mx32 = max(mx32, (uint32_t)(f < 0 ? -f : f));
             }
+            r = nxt + 1;
+            spec &= spec - 1;
         }
+        K += H * (Acc)cbt - a * (Acc)nt;
         nonempty += cnt;
         __syncwarp();
     }

@@ -9,9 +9,8 @@
 // per sample; otherwise values and 16-bit labels move separately.  The first read
 // also counts the first digit, and each pass counts the next one while it ranks.
 //
-// Within a 4096-sample tile, each warp ranks its 256 samples by digit-peer masks built
-// from eight ballots (stable: item-major, then lane order), per-warp digit counts are scanned across
-// warps, the tile is staged in shared memory in sorted order and written out so
+// Within a 4096-sample tile, each warp ranks its 256 samples by digit-peer masks
+// (stable: item-major, then lane order), per-warp digit counts are scanned across warps, the tile is staged in shared memory in sorted order and written out so
 // that consecutive positions of a digit go to consecutive addresses; a running
 // per-digit base carries the order across tiles.  The last step writes the labels
 // in value order to labA and the start of every run of equal values.
@@ -53,9 +52,14 @@ __device__ void scan256(const uint32_t *s_in, uint32_t *s_out, uint32_t *s_tmp) 
     __syncthreads();
 }
 
-// Lanes of vm holding the same 8-bit digit as this lane, from eight ballots (the result of
-// match.any, at a fraction of its cost).  Every lane of the warp must call it.
+// Lanes of vm holding the same 8-bit digit as this lane.  Every lane of the warp must call it.
+// match.any costs grow with the number of distinct digits in the warp (measured on B300:
+// eight ballots cost as much as match.any over about 14 distinct digits, and match.any over
+// one digit a tenth of that).  Latency digits within one warp usually span a narrow range, so
+// match.any is taken when the range is below 12 and the eight ballots otherwise.
 __device__ __forceinline__ unsigned digit_peers(uint32_t dg, unsigned vm) {
+    const uint32_t dmin = __reduce_min_sync(kFull, dg), dmax = __reduce_max_sync(kFull, dg);
+    if (dmax - dmin < 12u) return __match_any_sync(kFull, dg) & vm;
     unsigned peers = vm;
 #pragma unroll
     for (int b = 0; b < 8; b++) {
@@ -317,6 +321,9 @@ sort_series_kernel(const uint32_t *__restrict__ samples, SeriesDesc *__restrict_
         desc[s].nruns = (int32_t)count;
         const uint32_t km = fk[N / 2];
         desc[s].median = comp ? km >> 16 : km;
+        const uint32_t k50 = fk[(50 * (int64_t)N + 99) / 100 - 1], k95 = fk[(95 * (int64_t)N + 99) / 100 - 1];
+        desc[s].p50 = comp ? k50 >> 16 : k50;
+        desc[s].p95 = comp ? k95 >> 16 : k95;
     }
 }
 

@@ -303,3 +303,45 @@ def test_learned_mode_needs_weights():
     assert err.value.code == mt4g.EINVAL
     e.close()
     torch.cuda.synchronize()
+
+
+def test_trained_network_gains_over_untrained():
+    """What training buys: on held-out series of the training distribution, the trained weights
+    put the true change points inside their windows and are confident, so the learned path
+    evaluates fewer (split, value) pairs than with untrained weights.  Answers are identical
+    either way (certification is exact)."""
+    import os
+    weights = os.path.join(os.path.dirname(mt4g.__file__), "weights", "cnn_c2.bin")
+    b = synth.generate(2, 4, 512)
+    d = mt4g.to_device_samples(b.samples)
+    e = mt4g.Engine(0)
+    try:
+        full = e.ks_segment(d, b.offsets, b.steps, 1e-6, 1, 16, mode=mt4g.MODE_FULL)
+        full = [t.cpu().numpy() for t in full[1:6]]
+        assert e.wait() == mt4g.OK
+        evals_full = e.last_work()
+        e.set_option(mt4g.OPT_CONF_MIN_PPM, 0)  # both networks take the learned path everywhere
+        out = {}
+        for name in ("trained", "untrained"):
+            if name == "trained":
+                e.cnn_load(weights)
+            else:
+                e.cnn_init(2024)
+            win, conf = e.propose(d, b.offsets, b.steps, 3, 16)
+            win = win.cpu().numpy()
+            covered = np.mean([all(any(abs(int(c) - int(w)) <= 16 for w in win[s] if w >= 0)
+                                   for c in b.cps[s, :b.ncp[s]]) for s in range(512)])
+            r = e.ks_segment(d, b.offsets, b.steps, 1e-6, 1, 16, mode=mt4g.MODE_LEARNED)
+            res = [t.cpu().numpy() for t in r[1:6]]
+            assert e.wait() == mt4g.OK
+            for a, c in zip(full, res):
+                assert np.array_equal(a, c)
+            out[name] = {"covered": covered, "conf": float(conf.float().mean().item()),
+                         "evals": e.last_work(), "stats": e.learned_stats()}
+    finally:
+        e.close()
+    tr, un = out["trained"], out["untrained"]
+    msg = (out, evals_full)
+    assert tr["covered"] >= 0.95 and un["covered"] < 0.5, msg
+    assert tr["conf"] >= 0.9 > un["conf"], msg
+    assert tr["evals"] < un["evals"] < evals_full * 1.5, msg

@@ -277,3 +277,23 @@ def test_bounded_wait_expires_and_context_survives(eng):
     b = synth.generate(1, 0, 1)
     check_scan(eng, b)
     check_segment(eng, b, 1e-6)
+
+
+# ------------------------------------------------------------------ latency statistics (Sec. IV-C)
+
+def test_latency_stats_match_oracle(eng):
+    """mean, p50, p95 and std: the same IEEE rounding steps on both sides, so bit-equal."""
+    rng = np.random.default_rng(41)
+    series = [rng.integers(0, int(rng.integers(2, 2**32)), size=(int(rng.integers(2, 300)), int(rng.integers(1, 70))),
+                           dtype=np.uint64).astype(np.uint32) for _ in range(60)]
+    series += [np.full((3, 5), 2**32 - 1, np.uint32), np.array([[7] * 6, [19] * 6], np.uint32),
+               np.array([[5], [9]], np.uint32), rng.integers(2**31, 2**32, size=(4096, 8), dtype=np.uint64).astype(np.uint32)]
+    b2 = synth.generate(2, 1, 16)
+    series += [b2.series(s) for s in range(16)]
+    b = synth.from_arrays(series)
+    mean, p50, p95, std = [t.cpu().numpy() for t in eng.latency_stats(mt4g.to_device_samples(b.samples),
+                                                                        b.offsets, b.steps)]
+    om, o50, o95, ostd = oracle.latency_stats(b.samples, b.offsets, b.steps)
+    assert np.array_equal(p50.view(np.uint32), o50) and np.array_equal(p95.view(np.uint32), o95)
+    assert np.array_equal(mean, om), np.nonzero(mean != om)
+    assert np.array_equal(std, ostd), np.nonzero(std != ostd)

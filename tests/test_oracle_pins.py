@@ -365,3 +365,29 @@ def test_config1_golden_fixture():
     k, num, den, p = oracle.ks_scan(b.samples, b.offsets, b.steps)
     assert (int(k[0]), int(num[0]), int(den[0]), float(p[0])) == \
         (g["scan"]["k"], g["scan"]["num"], g["scan"]["den"], g["scan"]["p"])
+
+
+# ------------------------------------------------------------------ latency statistics (Sec. IV-C)
+
+def test_latency_stats_against_numpy(rng):
+    series = [rng.integers(1, 5000, size=(int(rng.integers(2, 40)), int(rng.integers(1, 30))), dtype=np.uint32)
+              for _ in range(30)]
+    b = synth.from_arrays(series)
+    mean, p50, p95, std = oracle.latency_stats(b.samples, b.offsets, b.steps)
+    for s, x in enumerate(series):
+        v = x.ravel().astype(np.float64)
+        assert p50[s] == np.percentile(x.ravel(), 50, method="inverted_cdf")
+        assert p95[s] == np.percentile(x.ravel(), 95, method="inverted_cdf")
+        assert abs(mean[s] - v.mean()) <= 1e-15 * v.mean()
+        assert abs(std[s] - v.std()) <= 1e-12 * max(v.std(), 1.0)
+
+
+def test_latency_stats_closed_forms():
+    big = np.full((4, 8), 2**32 - 1, np.uint32)            # naive FP64 sums of squares would not cancel
+    two = np.array([[7] * 6, [19] * 6], np.uint32)          # half 7, half 19
+    one = np.array([[5], [5]], np.uint32)
+    b = synth.from_arrays([big, two, one])
+    mean, p50, p95, std = oracle.latency_stats(b.samples, b.offsets, b.steps)
+    assert mean[0] == float(2**32 - 1) and std[0] == 0.0 and p50[0] == p95[0] == 2**32 - 1
+    assert mean[1] == 13.0 and std[1] == 6.0 and p50[1] == 7 and p95[1] == 19
+    assert mean[2] == 5.0 and std[2] == 0.0 and p50[2] == p95[2] == 5
