@@ -47,6 +47,11 @@ WORKLOADS = {
     "uneven": (3, 2, 16384, False, "plain full segmentation, 16384 uneven series, T 32..4096, m 8..256"),
 }
 LAUNCHES = {False: 4, True: 14}  # our kernels per call (plain / learned)
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch, per series, from the ncu
+# captures summarised in profiles/ (queue_kernel_plain_1024x512x128.md,
+# sort_series_kernel_1024x512x128.md); keyed by (workload, stage).  Only workloads whose kernels
+# were captured as they are now appear here; the others report null.
+NCU_TRAFFIC_PER_SERIES = {("plain", "queue"): 540.076288e6 / 1024, ("plain", "sort"): 1306.98496e6 / 1024}
 STAGES = ["upload", "sort", "proposals", "queue", "collect"]
 
 
@@ -119,10 +124,14 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- oracle timing
 
-def oracle_sample(args):
+def oracle_sample(args, baseline=False):
+    """A bounded, deterministic sample of the workload for the oracle: every k-th series.  The
+    reference arm times it once per step (a few seconds each); the CPU baseline beside the GPU
+    line times a larger one once (about 10-20 s on 16 host cores)."""
     cfg, seed, S, _, _ = WORKLOADS[args.workload]
     import synth
-    n = {"learned": 1024, "plain": 96, "uneven": 256}[args.workload]
+    n = ({"learned": 4096, "plain": 1024, "uneven": 1024} if baseline else
+         {"learned": 1024, "plain": 96, "uneven": 256})[args.workload]
     stride = max(1, S // n)
     idx = np.arange(0, S, stride)[:n]
     if cfg == 3:  # keep the sample's CPU time bounded: the oracle is O(T N) per segment
@@ -273,7 +282,7 @@ def main():
     line["e2e"] = {"value": S * world * e_steps / te, "unit": "series/s", "h2d_bytes_per_step": int(h2d),
                    "d2h_bytes_per_step": int(d2h), "steps": e_steps}
 
-    # ---------------- roofline of the dominant kernel
+    # ---------------- rooflines: every stage's kernel against its bound; the dominant one is `roofline`
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -284,32 +293,41 @@ def main():
     ms = dict(zip(STAGES, np.asarray(stages).mean(axis=0).tolist()))
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_mhz = (clk or {}).get("sm_mhz") or 2032.0
-    if ms["queue"] >= ms["sort"] and ms["queue"] >= ms["proposals"]:
-        ops = 4.0 * evals
-        achieved = ops / (ms["queue"] / 1e3) / 1e12
-        peak = sms * 128 * sm_mhz * 1e6 / 1e12
-        roof = {"kernel": "queue_kernel (exact scans, p-values, segmentation)", "bound": "alu",
-                "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak, "traffic": None,
-                "algorithmic_units": f"{evals:.4g} (split, distinct value) evaluations x 4 int ops",
-                "peak_source": f"{sms} SMs x 128 INT32 lanes x {sm_mhz:.0f} MHz (median SM clock under load)"}
-    elif ms["sort"] >= ms["proposals"]:
-        byts = 10.0 * Ntot
-        achieved = byts / (ms["sort"] / 1e3) / 1e9
-        roof = {"kernel": "sort_series_kernel (radix sort + run table)", "bound": "hbm", "achieved": achieved,
-                "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
-                "algorithmic_units": f"{Ntot} samples x 10 B (4 B read + 6 B sorted value/label written)",
-                "peak_source": f"{hbm_src} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
-    else:
-        byts = 4.0 * Ntot
-        achieved = byts / (ms["proposals"] / 1e3) / 1e9
-        roof = {"kernel": "summaries + CNN + windows", "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
-                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
-                "algorithmic_units": f"{Ntot} samples x 4 B read", "peak_source": f"{hbm_src} HBM copy bandwidth"}
+    nominal_int = sms * 128 * sm_mhz * 1e6 / 1e12
+    int_peak = mt4g.int32_peak(local)
+    rooflines = {
+        "queue": {"kernel": "queue_kernel (exact scans, p-values, segmentation)", "bound": "alu",
+                  "achieved": 4.0 * evals / (ms["queue"] / 1e3) / 1e12, "peak": int_peak, "unit": "Tops/s",
+                  "traffic": None,
+                  "algorithmic_units": f"{evals:.4g} (split, distinct value) evaluations x 4 int ops",
+                  "peak_source": "measured: mt4g_int32_peak (the scan's 4-op step mix on every SM, this run)",
+                  "nominal_peak": nominal_int,
+                  "nominal_source": f"{sms} SMs x 128 INT32 lanes x {sm_mhz:.0f} MHz (median SM clock under load)"},
+        "sort": {"kernel": "sort_series_kernel (radix sort + run table)", "bound": "hbm",
+                 "achieved": 10.0 * Ntot / (ms["sort"] / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                 "traffic": None,
+                 "algorithmic_units": f"{Ntot} samples x 10 B (4 B read + 6 B sorted value/label written)",
+                 "peak_source": f"{hbm_src} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
+    }
+    if learned:
+        rooflines["proposals"] = {"kernel": "summaries + CNN + windows", "bound": "hbm",
+                                  "achieved": 4.0 * Ntot / (ms["proposals"] / 1e3) / 1e9, "peak": hbm_peak,
+                                  "unit": "GB/s", "traffic": None,
+                                  "algorithmic_units": f"{Ntot} samples x 4 B read",
+                                  "peak_source": f"{hbm_src} HBM copy bandwidth"}
+    for k, r in rooflines.items():
+        r["frac"] = r["achieved"] / r["peak"]
+        per = NCU_TRAFFIC_PER_SERIES.get((args.workload, k))
+        r["traffic"] = per * S if per is not None else None
+    dominant = max(rooflines, key=lambda k: ms[k])
+    roof = dict(rooflines[dominant])
+    line["rooflines"] = {k: {kk: v[kk] for kk in ("kernel", "bound", "achieved", "peak", "unit", "frac", "traffic")}
+                         for k, v in rooflines.items()}
     roof["stage_ms"] = ms
     line["roofline"] = roof
     line["clocks"] = clk
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        sb, desc = oracle_sample(args)
+        sb, desc = oracle_sample(args, baseline=True)
         cores = os.cpu_count() or 1
         t = run_oracle(sb, cores)
         line["cpu_baseline"] = {"value": sb.S / t, "unit": "series/s", "cores": cores, "kind": "oracle",
