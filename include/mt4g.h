@@ -136,6 +136,24 @@ int mt4g_ks_segment(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offse
                     int32_t *cp_count, int32_t *cp_idx, int64_t *dnum, int64_t *dden, double *p,
                     int32_t *fallback, void *cuda_stream);
 
+/*
+ * mt4g_ks_segment with the samples in HOST memory (the same segmentation and results).
+ * The batch is cut into chunks of consecutive series of at most chunk_samples samples each
+ * (<= 0: 2^26; a longer series is a chunk by itself).  Chunk c + 1 is copied to the device on
+ * the context's copy stream while chunk c is segmented on cuda_stream, through two device
+ * staging buffers the context keeps, so the host-to-device transfer overlaps the computation;
+ * give samples_host in page-locked memory (cudaMallocHost / cudaHostRegister) for the copies
+ * to run asynchronously.  offsets/steps are HOST tables as for mt4g_ks_segment; the outputs
+ * are DEVICE arrays indexed by the global series number.  Asynchronous like every call:
+ * samples_host must stay valid and unchanged until mt4g_wait() returns, and mt4g_wait()
+ * reports the combined device-side status of all chunks.  CUDA-graph replay does not apply.
+ * No counterpart in the paper (it is the input path of a batched service).
+ */
+int mt4g_ks_segment_host(mt4g_ctx *ctx, const uint32_t *samples_host, const int64_t *offsets, const int32_t *steps,
+                         int64_t S, double alpha, int32_t min_seg, int32_t max_cp, int32_t mode,
+                         int64_t chunk_samples, int32_t *cp_count, int32_t *cp_idx, int64_t *dnum, int64_t *dden,
+                         double *p, int32_t *fallback, void *cuda_stream);
+
 /* ------------------------------------------------------------------ learned proposal
  *
  * The paper scans every index (Sec. IV-B-1 (4)) and notes that candidate change points

@@ -74,6 +74,7 @@ def load_library():
     L.mt4g_stage_times.argtypes = [vp, vp, i32]
     L.mt4g_int32_peak.argtypes = [ctypes.c_int, vp]
     L.mt4g_latency_stats.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp, vp, vp]
+    L.mt4g_ks_segment_host.argtypes = [vp, vp, vp, vp, i64, dbl, i32, i32, i32, i64, vp, vp, vp, vp, vp, vp, vp]
     L.mt4g_last_work.argtypes = [vp, vp]
     L.mt4g_summaries.argtypes = [vp, vp, vp, vp, i64, vp, vp]
     L.mt4g_cnn_init.argtypes = [vp, ctypes.c_uint64]
@@ -97,7 +98,7 @@ def exported_symbols():
             "mt4g_cnn_load", "mt4g_cnn_forward", "mt4g_cnn_grads", "mt4g_cnn_train_step", "mt4g_propose",
             "mt4g_learned_stats", "mt4g_ks_scan_noalloc", "mt4g_selftest_wait_timeout", "mt4g_critical_value",
             "mt4g_autotune", "mt4g_autotune_save", "mt4g_autotune_load", "mt4g_autotune_get",
-            "mt4g_int32_peak", "mt4g_latency_stats"]
+            "mt4g_int32_peak", "mt4g_latency_stats", "mt4g_ks_segment_host"]
 
 
 class ScanResult(NamedTuple):
@@ -261,6 +262,45 @@ class Engine:
                                      int(max_cp), mode, _dev_ptr(out.count, "count"), _dev_ptr(out.idx, "idx"),
                                      _dev_ptr(out.dnum, "dnum"), _dev_ptr(out.dden, "dden"), _dev_ptr(out.p, "p"),
                                      _dev_ptr(out.fallback, "fallback"), _stream_handle(stream))
+        self._check(rc)
+        status = OK
+        if sync:
+            status = self.wait()
+            if status not in (OK, ECAPACITY):
+                self._check(status)
+        return out._replace(rc=status)
+
+    def ks_segment_host(self, samples_host, offsets, steps, alpha: float, min_seg: int = 1, max_cp: int = 16,
+                        mode: int = MODE_FULL, chunk_samples: int = 0, stream=None, out=None, device=None,
+                        sync: bool = True) -> SegmentResult:
+        """mt4g_ks_segment_host: samples in host memory (a CPU tensor, page-locked for overlap, or a
+        numpy array), copied chunk by chunk while earlier chunks are segmented.  Outputs on the
+        device; samples_host must stay alive until wait()."""
+        import torch
+        offsets, steps = _host_tables(offsets, steps)
+        S = steps.shape[0]
+        if isinstance(samples_host, np.ndarray):
+            if samples_host.dtype not in (np.uint32, np.int32) or not samples_host.flags.c_contiguous:
+                raise Mt4gError(EINVAL, "host samples must be a contiguous uint32 array")
+            ptr = samples_host.ctypes.data_as(ctypes.c_void_p)
+        else:
+            if not isinstance(samples_host, torch.Tensor) or samples_host.is_cuda or not samples_host.is_contiguous():
+                raise Mt4gError(EINVAL, "host samples must be a contiguous CPU tensor or numpy array")
+            ptr = ctypes.c_void_p(samples_host.data_ptr())
+        dev = torch.device("cuda", self.device) if device is None else device
+        if out is None:
+            out = SegmentResult(0, torch.empty(S, dtype=torch.int32, device=dev),
+                                torch.empty((S, max_cp), dtype=torch.int32, device=dev),
+                                torch.empty((S, max_cp), dtype=torch.int64, device=dev),
+                                torch.empty((S, max_cp), dtype=torch.int64, device=dev),
+                                torch.empty((S, max_cp), dtype=torch.float64, device=dev),
+                                torch.empty(S, dtype=torch.int32, device=dev))
+        rc = self._L.mt4g_ks_segment_host(self._h, ptr, offsets.ctypes.data_as(ctypes.c_void_p),
+                                          steps.ctypes.data_as(ctypes.c_void_p), S, float(alpha), int(min_seg),
+                                          int(max_cp), mode, int(chunk_samples), _dev_ptr(out.count, "count"),
+                                          _dev_ptr(out.idx, "idx"), _dev_ptr(out.dnum, "dnum"),
+                                          _dev_ptr(out.dden, "dden"), _dev_ptr(out.p, "p"),
+                                          _dev_ptr(out.fallback, "fallback"), _stream_handle(stream))
         self._check(rc)
         status = OK
         if sync:

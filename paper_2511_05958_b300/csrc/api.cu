@@ -28,6 +28,18 @@ struct mt4g_ctx {
     size_t pin_bytes = 0;
     cudaEvent_t pin_free = nullptr;  // recorded after the last upload out of `pin`
     QueueHeader *h_hdr = nullptr;     // pinned: queue header (status, work) of the last call
+    QueueHeader *hdr_dst = nullptr;   // when set, finish_call copies the header here instead
+    // host-input segmentation (mt4g_ks_segment_host): two device staging buffers, a copy stream,
+    // and the per-chunk queue headers that mt4g_wait() combines
+    void *hin[2] = {nullptr, nullptr};
+    size_t hin_bytes = 0;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
+    cudaStream_t up_stream = nullptr;  // while set: table uploads go on this stream (the copy stream)
+    cudaEvent_t ev_up = nullptr;
+    QueueHeader *h_chunk_hdr = nullptr;  // pinned
+    int64_t chunk_hdr_cap = 0;
+    int64_t n_chunk_hdr = 0;             // headers of the last host-input call, combined by mt4g_wait
     cudaStream_t last_stream = nullptr;
     bool have_last = false;      // some call has enqueued work on last_stream
     bool last_enqueued = false;  // the most recent call enqueued work (its status is in h_hdr)
@@ -342,6 +354,18 @@ cudaError_t staged(mt4g_ctx *ctx, cudaStream_t st) {
     return ctx->capturing ? cudaSuccess : cudaEventRecord(ctx->pin_free, st);
 }
 
+// A call's host-to-device table uploads go on the call's stream, except during a host-input
+// call: there they go on its copy stream, queued in order with the chunk copies, because every
+// H2D copy of the device shares one copy engine and an upload behind the next chunk's copy would
+// hold up the current chunk.  uploads_done makes the call's stream wait for them.
+cudaStream_t upload_stream(const mt4g_ctx *ctx, cudaStream_t st) { return ctx->up_stream ? ctx->up_stream : st; }
+
+cudaError_t uploads_done(mt4g_ctx *ctx, cudaStream_t us, cudaStream_t st) {
+    if (us == st) return cudaSuccess;
+    cudaError_t e = cudaEventRecord(ctx->ev_up, us);
+    return e != cudaSuccess ? e : cudaStreamWaitEvent(st, ctx->ev_up, 0);
+}
+
 // Everything a call enqueues up to (and including) the work-queue kernel.
 int enqueue_pipeline(mt4g_ctx *ctx, const uint32_t *samples, Plan &P, RunParams &R, Buffers &B, cudaStream_t st) {
     size_t ready_off = 0;
@@ -407,14 +431,16 @@ int enqueue_pipeline(mt4g_ctx *ctx, const uint32_t *samples, Plan &P, RunParams 
     const size_t o_ready = o;
     if (bytes_ready) memcpy(h + o, P.item_base.data(), bytes_ready);
 
-    CUDA_TRY(ctx, cudaMemcpyAsync(B.q, h, bytes_hdr, cudaMemcpyHostToDevice, st));
-    if (bytes_desc) CUDA_TRY(ctx, cudaMemcpyAsync(B.desc, h + o_desc, bytes_desc, cudaMemcpyHostToDevice, st));
-    if (bytes_raw) CUDA_TRY(ctx, cudaMemcpyAsync(B.raw_desc, h + o_raw, bytes_raw, cudaMemcpyHostToDevice, st));
-    if (bytes_order) CUDA_TRY(ctx, cudaMemcpyAsync(B.order, h + o_order, bytes_order, cudaMemcpyHostToDevice, st));
-    if (bytes_items) CUDA_TRY(ctx, cudaMemcpyAsync(B.qorder, h + o_items, bytes_items, cudaMemcpyHostToDevice, st));
+    const cudaStream_t us = upload_stream(ctx, st);
+    CUDA_TRY(ctx, cudaMemcpyAsync(B.q, h, bytes_hdr, cudaMemcpyHostToDevice, us));
+    if (bytes_desc) CUDA_TRY(ctx, cudaMemcpyAsync(B.desc, h + o_desc, bytes_desc, cudaMemcpyHostToDevice, us));
+    if (bytes_raw) CUDA_TRY(ctx, cudaMemcpyAsync(B.raw_desc, h + o_raw, bytes_raw, cudaMemcpyHostToDevice, us));
+    if (bytes_order) CUDA_TRY(ctx, cudaMemcpyAsync(B.order, h + o_order, bytes_order, cudaMemcpyHostToDevice, us));
+    if (bytes_items) CUDA_TRY(ctx, cudaMemcpyAsync(B.qorder, h + o_items, bytes_items, cudaMemcpyHostToDevice, us));
     if (bytes_ready)
-        CUDA_TRY(ctx, cudaMemcpyAsync(B.item_base, h + o_ready, bytes_ready, cudaMemcpyHostToDevice, st));
-    CUDA_TRY(ctx, staged(ctx, st));
+        CUDA_TRY(ctx, cudaMemcpyAsync(B.item_base, h + o_ready, bytes_ready, cudaMemcpyHostToDevice, us));
+    CUDA_TRY(ctx, staged(ctx, us));
+    CUDA_TRY(ctx, uploads_done(ctx, us, st));
     if (!P.learned)
         CUDA_TRY(ctx, launch_init_items(B.desc, B.qorder, B.item_base, P.S, P.min_seg, B.items, B.ready, B.gcount,
                                         epoch, st));
@@ -455,7 +481,8 @@ int finish_call(mt4g_ctx *ctx, Buffers &B, cudaStream_t st) {
         ctx->ring_pos = (ctx->ring_pos + 1) % mt4g_ctx::kTimingRing;
         ctx->ring_count = std::min(ctx->ring_count + 1, mt4g_ctx::kTimingRing);
     }
-    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_hdr, B.q, sizeof(QueueHeader), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->hdr_dst ? ctx->hdr_dst : ctx->h_hdr, B.q, sizeof(QueueHeader),
+                                  cudaMemcpyDeviceToHost, st));
     ctx->last_stream = st;
     ctx->have_last = true;
     ctx->last_enqueued = true;
@@ -466,6 +493,7 @@ int begin_call(mt4g_ctx *ctx) {
     if (!ctx) return MT4G_EINVAL;
     ctx->err.clear();
     ctx->last_enqueued = false;
+    ctx->n_chunk_hdr = 0;
     CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     return MT4G_OK;
 }
@@ -515,6 +543,18 @@ void mt4g_destroy(mt4g_ctx *c) {
         cudaEventDestroy(c->graph_in);
         cudaEventDestroy(c->graph_out);
     }
+    if (c->copy_stream) {
+        cudaStreamSynchronize(c->copy_stream);
+        cudaStreamDestroy(c->copy_stream);
+        for (int b = 0; b < 2; b++) {
+            cudaEventDestroy(c->ev_copied[b]);
+            cudaEventDestroy(c->ev_free[b]);
+        }
+        cudaEventDestroy(c->ev_up);
+    }
+    for (int b = 0; b < 2; b++)
+        if (c->hin[b]) cudaFree(c->hin[b]);
+    if (c->h_chunk_hdr) cudaFreeHost(c->h_chunk_hdr);
     if (c->cnn_alloc) cudaFree(c->cnn.master);
     if (c->pin) cudaFreeHost(c->pin);
     if (c->h_hdr) cudaFreeHost(c->h_hdr);
@@ -579,6 +619,19 @@ int mt4g_wait(mt4g_ctx *c) {
     CUDA_TRY(c, cudaSetDevice(c->device));
     CUDA_TRY(c, cudaStreamSynchronize(c->last_stream));
     if (!c->last_enqueued) return MT4G_OK;
+    if (c->n_chunk_hdr > 0) {  // a host-input call: combine its chunks' headers
+        QueueHeader sum{};
+        for (int64_t i = 0; i < c->n_chunk_hdr; i++) {
+            const QueueHeader &h = c->h_chunk_hdr[i];
+            sum.status |= h.status;
+            sum.evals += h.evals;
+            sum.certified += h.certified;
+            sum.refined += h.refined;
+            sum.rec_next += h.rec_next;
+        }
+        *c->h_hdr = sum;
+        c->n_chunk_hdr = 0;
+    }
     const int32_t st = c->h_hdr->status;
     if (st & kStatusTimeout) return fail(c, MT4G_ETIMEOUT, "a bounded device-side wait expired");
     if (st & kStatusQueueFull) return fail(c, MT4G_ECAPACITY, "work queue capacity exceeded");
@@ -822,6 +875,95 @@ int mt4g_ks_segment(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offse
         });
 }
 
+int mt4g_ks_segment_host(mt4g_ctx *ctx, const uint32_t *samples_host, const int64_t *offsets, const int32_t *steps,
+                         int64_t S, double alpha, int32_t min_seg, int32_t max_cp, int32_t mode,
+                         int64_t chunk_samples, int32_t *cp_count, int32_t *cp_idx, int64_t *dnum, int64_t *dden,
+                         double *p, int32_t *fallback, void *cuda_stream) {
+    int rc = begin_call(ctx);
+    if (rc) return rc;
+    if (S < 0 || (S > 0 && (!offsets || !steps))) return fail(ctx, MT4G_EINVAL, "bad host tables");
+    if (S == 0) return MT4G_OK;
+    if (!samples_host) return fail(ctx, MT4G_EINVAL, "NULL host sample pointer");
+    if (offsets[0] != 0) return fail(ctx, MT4G_EINVAL, "offsets[0] must be 0");
+    for (int64_t s = 0; s < S; s++)
+        if (offsets[s + 1] < offsets[s]) return fail(ctx, MT4G_EINVAL, "offsets must be non-decreasing");
+    if (chunk_samples <= 0) chunk_samples = (int64_t)1 << 26;
+    // chunks: consecutive series up to chunk_samples samples (a larger series is a chunk alone)
+    std::vector<int64_t> first{0};
+    for (int64_t s = 1; s < S; s++)
+        if (offsets[s + 1] - offsets[first.back()] > chunk_samples) first.push_back(s);
+    first.push_back(S);
+    const int64_t nchunks = (int64_t)first.size() - 1;
+    int64_t max_chunk = 0;
+    for (int64_t c = 0; c < nchunks; c++) max_chunk = std::max(max_chunk, offsets[first[c + 1]] - offsets[first[c]]);
+    const size_t need = (size_t)max_chunk * sizeof(uint32_t);
+    // staging buffers, copy stream, events, per-chunk headers (grown on demand)
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (need > ctx->hin_bytes) {
+        CUDA_TRY(ctx, cudaDeviceSynchronize());
+        for (int b = 0; b < 2; b++) {
+            if (ctx->hin[b]) cudaFree(ctx->hin[b]);
+            ctx->hin[b] = nullptr;
+        }
+        ctx->hin_bytes = 0;
+        for (int b = 0; b < 2; b++)
+            if (cudaMalloc(&ctx->hin[b], need) != cudaSuccess)
+                return fail(ctx, MT4G_ENOMEM, "cannot allocate %zu bytes of input staging", need);
+        ctx->hin_bytes = need;
+    }
+    if (!ctx->copy_stream) {
+        CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+        for (int b = 0; b < 2; b++) {
+            CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->ev_copied[b], cudaEventDisableTiming));
+            CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->ev_free[b], cudaEventDisableTiming));
+        }
+        CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->ev_up, cudaEventDisableTiming));
+    }
+    if (nchunks > ctx->chunk_hdr_cap) {
+        if (ctx->have_last) CUDA_TRY(ctx, cudaStreamSynchronize(ctx->last_stream));
+        if (ctx->h_chunk_hdr) cudaFreeHost(ctx->h_chunk_hdr);
+        ctx->h_chunk_hdr = nullptr;
+        ctx->chunk_hdr_cap = 0;
+        if (cudaMallocHost(&ctx->h_chunk_hdr, (size_t)nchunks * sizeof(QueueHeader)) != cudaSuccess)
+            return fail(ctx, MT4G_ENOMEM, "cannot allocate pinned chunk headers");
+        ctx->chunk_hdr_cap = nchunks;
+    }
+    // the previous user of the staging buffers must be done with them
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->copy_stream));
+    if (ctx->have_last && ctx->last_stream != st) CUDA_TRY(ctx, cudaStreamSynchronize(ctx->last_stream));
+    for (int b = 0; b < 2; b++) CUDA_TRY(ctx, cudaEventRecord(ctx->ev_free[b], st));
+    std::vector<int64_t> loc;
+    for (int64_t c = 0; c < nchunks; c++) {
+        const int b = (int)(c & 1);
+        const int64_t s0 = first[c], n = first[c + 1] - first[c];
+        const int64_t base = offsets[s0], cnt = offsets[first[c + 1]] - base;
+        // copy chunk c while chunk c - 1 is processed; buffer b is free once chunk c - 2 is done
+        CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_free[b], 0));
+        CUDA_TRY(ctx, cudaMemcpyAsync(ctx->hin[b], samples_host + base, (size_t)cnt * sizeof(uint32_t),
+                                      cudaMemcpyHostToDevice, ctx->copy_stream));
+        CUDA_TRY(ctx, cudaEventRecord(ctx->ev_copied[b], ctx->copy_stream));
+        CUDA_TRY(ctx, cudaStreamWaitEvent(st, ctx->ev_copied[b], 0));
+        loc.assign(offsets + s0, offsets + s0 + n + 1);
+        for (auto &o : loc) o -= base;
+        // the chunk's table uploads (on the copy stream, after this copy) overwrite the context's
+        // workspace: the previous chunk must be done with it
+        if (c > 0) CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_free[b ^ 1], 0));
+        ctx->hdr_dst = ctx->h_chunk_hdr + c;
+        ctx->up_stream = ctx->copy_stream;
+        rc = segment_body(ctx, (const uint32_t *)ctx->hin[b], loc.data(), steps + s0, n, alpha, min_seg, max_cp, mode,
+                          cp_count + s0, max_cp ? cp_idx + s0 * max_cp : cp_idx, max_cp ? dnum + s0 * max_cp : dnum,
+                          max_cp ? dden + s0 * max_cp : dden, max_cp ? p + s0 * max_cp : p,
+                          fallback ? fallback + s0 : nullptr, (void *)st);
+        ctx->hdr_dst = nullptr;
+        ctx->up_stream = nullptr;
+        if (rc) return rc;
+        CUDA_TRY(ctx, cudaEventRecord(ctx->ev_free[b], st));
+    }
+    ctx->n_chunk_hdr = nchunks;
+    ctx->last_enqueued = true;
+    return MT4G_OK;
+}
+
 int mt4g_stage_times(mt4g_ctx *c, double *ms_out, int32_t max_calls) {
     if (!c || (max_calls > 0 && !ms_out)) return MT4G_EINVAL;
     if (!c->timing) return fail(c, MT4G_EINVAL, "stage timing is off (MT4G_OPT_STAGE_TIMING)");
@@ -938,10 +1080,12 @@ int upload_cnn_tables(mt4g_ctx *c, const std::vector<SeriesDesc> &desc, CnnBuffe
     if (rc) return rc;
     memcpy(h, desc.data(), S * sizeof(SeriesDesc));
     memcpy(h + S * sizeof(SeriesDesc), tb.data(), S * sizeof(int64_t));
-    CUDA_TRY(c, cudaMemcpyAsync(B.desc, h, S * sizeof(SeriesDesc), cudaMemcpyHostToDevice, st));
+    const cudaStream_t us = upload_stream(c, st);
+    CUDA_TRY(c, cudaMemcpyAsync(B.desc, h, S * sizeof(SeriesDesc), cudaMemcpyHostToDevice, us));
     CUDA_TRY(c, cudaMemcpyAsync(B.tiles_before, h + S * sizeof(SeriesDesc), S * sizeof(int64_t),
-                                cudaMemcpyHostToDevice, st));
-    CUDA_TRY(c, staged(c, st));
+                                cudaMemcpyHostToDevice, us));
+    CUDA_TRY(c, staged(c, us));
+    CUDA_TRY(c, uploads_done(c, us, st));
     return MT4G_OK;
 }
 

@@ -122,28 +122,44 @@ __global__ void __launch_bounds__(128) conv32_kernel(const TIn *__restrict__ in,
     }
 }
 
-// Last layer, 32 -> 1: logits[row] = b + sum_{d,i} W4[d][i] a3[row + d - 2][i].
+// Last layer, 32 -> 1: logits[row] = b + sum_{d,i} W4[d][i] a3[row + d - 2][i].  The tile's
+// kTile + 4 activation rows (64 B each) are staged in shared memory with 16-byte loads first, so
+// every row is read from memory once.
 __global__ void __launch_bounds__(kTile) conv_out_kernel(const __nv_bfloat16 *__restrict__ a3,
                                                          const float *__restrict__ W4, const float *__restrict__ b4,
                                                          float *__restrict__ logits,
                                                          const SeriesDesc *__restrict__ desc,
                                                          const int64_t *__restrict__ tiles_before, int64_t S) {
     __shared__ float w[5 * 32];
+    __shared__ __align__(16) uint4 xs[(kTile + 4) * 4];  // 8 BF16 channels per uint4
     const int64_t tile = blockIdx.x;
     const int64_t s = find_series(tiles_before, S, tile);
     const SeriesDesc d = desc[s];
-    const int t = (int)(tile - tiles_before[s]) * kTile + threadIdx.x;
+    const int t0 = (int)(tile - tiles_before[s]) * kTile;
+    const int64_t r0 = row_base(d, s) + t0;  // padded row of the window start of position t0
+    const int nrows = min(kTile + 4, d.T + 4 - t0);
+    const uint4 *src = reinterpret_cast<const uint4 *>(a3 + r0 * 32);
+    for (int e = threadIdx.x; e < (kTile + 4) * 4; e += kTile) xs[e] = e < nrows * 4 ? src[e] : make_uint4(0, 0, 0, 0);
     for (int e = threadIdx.x; e < 160; e += kTile) w[e] = W4[e];
     __syncthreads();
+    const int t = t0 + threadIdx.x;
     if (t >= d.T) return;
-    const int64_t row = row_base(d, s) + 2 + t;
     float acc = b4[0];
+#pragma unroll
     for (int dd = 0; dd < 5; dd++) {
-        const __nv_bfloat16 *x = a3 + (row + dd - 2) * 32;
-#pragma unroll 8
-        for (int i = 0; i < 32; i++) acc = fmaf(bf(x[i]), w[dd * 32 + i], acc);
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            const uint4 v = xs[(threadIdx.x + dd) * 4 + c];
+            const uint32_t u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int h = 0; h < 4; h++) {
+                const float lo = __uint_as_float(u[h] << 16), hi = __uint_as_float(u[h] & 0xffff0000u);
+                acc = fmaf(lo, w[dd * 32 + c * 8 + 2 * h], acc);
+                acc = fmaf(hi, w[dd * 32 + c * 8 + 2 * h + 1], acc);
+            }
+        }
     }
-    logits[row] = acc;
+    logits[r0 + 2 + threadIdx.x] = acc;
 }
 
 // dA3[row][i] = [a3 > 0] sum_d W4[d][i] g[row + 2 - d]  (gradient through the last layer)

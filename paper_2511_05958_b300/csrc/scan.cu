@@ -704,8 +704,14 @@ __device__ __noinline__ void certify_segment(const RunParams &P, const SeriesDes
         if (lane == 0) atomicAdd(&P.q->certified, 1ull);
         return;
     }
-    // refine the open gaps: slices of 32 splits over a + 1 .. b - 1
-    const int ns = open ? (gb - ga - 1 + 31) / 32 : 0;
+    // refine the open gaps: consecutive open gaps form one range a + 1 .. b - 1 (the grid splits
+    // between them are scanned again, which changes nothing), cut into slices of 32 splits, so
+    // that narrow gaps do not leave most lanes of a slice idle
+    const bool owner = open && (lane == 0 || !((openm >> (lane - 1)) & 1u));
+    const unsigned after = lane < 31 ? ~openm & (0xffffffffu << (lane + 1)) : 0u;
+    const int last = after ? __ffs(after) - 2 : 31;  // last open gap of this lane's run
+    const int rb = __shfl_sync(kFull, gb, last);
+    const int ns = owner ? (rb - ga - 1 + 31) / 32 : 0;
     int incl = ns;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -725,7 +731,7 @@ __device__ __noinline__ void certify_segment(const RunParams &P, const SeriesDes
     const int first = incl - ns;
     for (int i = 0; i < ns; i++)
         put_item(P, base + first + i,
-                 WorkItem{it.series, lo, hi, first + i, kRefine | (tot << 8), ga + 1 + 32 * i, gb - 1, it.rec});
+                 WorkItem{it.series, lo, hi, first + i, kRefine | (tot << 8), ga + 1 + 32 * i, rb - 1, it.rec});
     if (lane == 0) P.gcount[base] = 0;
     __threadfence();
     for (int i = 0; i < ns; i++) st_release_u32((uint32_t *)P.ready + base + first + i, epoch);

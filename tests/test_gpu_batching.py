@@ -96,3 +96,35 @@ def test_autotune_keeps_results_and_roundtrips(eng, tmp_path):
     for T, m in zip(bb.steps, bb.m):
         assert e2.autotune_get(int(T), int(m)) == eng.autotune_get(int(T), int(m))
     e2.close()
+
+
+def test_host_input_chunks_match_device_input(eng):
+    """mt4g_ks_segment_host: chunked copies overlapped with segmentation give the device-input
+    answers, for chunk sizes from one series per chunk to one chunk, in full and learned mode;
+    the capacity status of a middle chunk reaches mt4g_wait()."""
+    import torch
+    b = synth.generate(2, 44, 40)
+    d = mt4g.to_device_samples(b.samples)
+    host = torch.from_numpy(b.samples.view(np.int32)).pin_memory()
+    eng.cnn_init(8)
+    eng.set_option(mt4g.OPT_CONF_MIN_PPM, 0)
+    try:
+        for mode in (mt4g.MODE_FULL, mt4g.MODE_LEARNED):
+            _, ref = _seg(eng, d, b, mode=mode)
+            for chunk in (1, 3 * 65536 + 1, 10**9):
+                r = eng.ks_segment_host(host, b.offsets, b.steps, 1e-6, 1, 16, mode=mode, chunk_samples=chunk)
+                _same(ref, [t.cpu().numpy() for t in r[1:6]])
+        # numpy input, ragged series, a capacity overflow in one chunk only
+        rng = np.random.default_rng(5)
+        series = [rng.integers(0, 50, size=(int(rng.integers(2, 60)), int(rng.integers(1, 9))), dtype=np.uint32)
+                  for _ in range(30)]
+        series[17] = np.repeat(np.arange(40, dtype=np.uint32)[:, None] * 1000, 64, axis=1)  # 39 change points
+        bb = synth.from_arrays(series)
+        full = eng.ks_segment(mt4g.to_device_samples(bb.samples), bb.offsets, bb.steps, 1e-6, 1, 8)
+        assert full.rc == mt4g.ECAPACITY
+        hr = eng.ks_segment_host(bb.samples, bb.offsets, bb.steps, 1e-6, 1, 8, chunk_samples=200)
+        assert hr.rc == mt4g.ECAPACITY
+        for a, c in zip(full[1:6], hr[1:6]):
+            assert np.array_equal(a.cpu().numpy(), c.cpu().numpy())
+    finally:
+        eng.set_option(mt4g.OPT_CONF_MIN_PPM, 900000)
