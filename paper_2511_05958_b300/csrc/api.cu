@@ -1326,7 +1326,7 @@ int mt4g_cnn_forward(mt4g_ctx *c, const uint16_t *feat, const int32_t *steps, in
     rc = zero_pads(c, B, S, false, st);
     if (rc) return rc;
     CUDA_TRY(c, cnn_prepare(c->cnn, st));
-    CUDA_TRY(c, cnn_forward(c->cnn, feat, B.A, B.desc, B.tiles_before, S, ntiles, st));
+    CUDA_TRY(c, cnn_forward(c->cnn, feat, B.A, B.desc, B.tiles_before, S, ntiles, c->wait_limit_ns, nullptr, st));
     c->last_stream = st;
     c->have_last = true;
     return MT4G_OK;
@@ -1353,7 +1353,7 @@ static int cnn_fwd_bwd(mt4g_ctx *c, const uint16_t *feat, int32_t T, int64_t Bn,
     rc = zero_pads(c, B, Bn, true, st);
     if (rc) return rc;
     CUDA_TRY(c, cnn_prepare(c->cnn, st));
-    CUDA_TRY(c, cnn_forward(c->cnn, feat, B.A, B.desc, B.tiles_before, Bn, ntiles, st));
+    CUDA_TRY(c, cnn_forward(c->cnn, feat, B.A, B.desc, B.tiles_before, Bn, ntiles, c->wait_limit_ns, nullptr, st));
     CUDA_TRY(c, cnn_backward(c->cnn, feat, B.A, cp_count, cp_idx, max_cp, B.desc, Bn, T, grad_out,
                              loss_out ? loss_out : c->cnn.loss, st));
     c->last_stream = st;
@@ -1414,7 +1414,8 @@ int mt4g_propose(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets,
     if (rc) return rc;
     CUDA_TRY(ctx, launch_summaries(samples, B.desc, S, C.feat, st));
     CUDA_TRY(ctx, cnn_prepare(ctx->cnn, st));
-    CUDA_TRY(ctx, cnn_forward(ctx->cnn, C.feat, C.A, B.desc, C.tiles_before, S, ntiles, st));
+    CUDA_TRY(ctx, cnn_forward(ctx->cnn, C.feat, C.A, B.desc, C.tiles_before, S, ntiles, ctx->wait_limit_ns,
+                              &B.q->status, st));
     CUDA_TRY(ctx, launch_propose(C.A.logits, B.desc, S, n_win, half_width, win_center, conf, st));
     mark(ctx, 3, st);
     mark(ctx, 4, st);
@@ -1447,7 +1448,8 @@ int enqueue_proposals(mt4g_ctx *ctx, const uint32_t *samples, Plan &P, Buffers &
     if (rc) return rc;
     CUDA_TRY(ctx, launch_summaries(samples, B.desc, S, C.feat, st));
     CUDA_TRY(ctx, cnn_prepare(ctx->cnn, st));
-    CUDA_TRY(ctx, cnn_forward(ctx->cnn, C.feat, C.A, B.desc, C.tiles_before, S, ntiles, st));
+    CUDA_TRY(ctx, cnn_forward(ctx->cnn, C.feat, C.A, B.desc, C.tiles_before, S, ntiles, ctx->wait_limit_ns,
+                              &B.q->status, st));
     CUDA_TRY(ctx, launch_propose(C.A.logits, B.desc, S, ctx->n_win, ctx->half, C.win, C.conf, st));
     R.win_center = C.win;
     R.n_win = ctx->n_win;

@@ -366,18 +366,23 @@ cudaError_t cnn_prepare(const CnnState &W, cudaStream_t st) {
 }
 
 cudaError_t cnn_forward(const CnnState &W, const uint16_t *feat, const CnnActs &A, const SeriesDesc *desc,
-                        const int64_t *tiles_before, int64_t S, int64_t ntiles, cudaStream_t st) {
+                        const int64_t *tiles_before, int64_t S, int64_t ntiles, long long wait_limit_ns,
+                        int32_t *status, cudaStream_t st) {
     if (ntiles <= 0) return cudaSuccess;
     const __nv_bfloat16 *x0 = reinterpret_cast<const __nv_bfloat16 *>(feat);
     const float *u = W.used;
-    conv32_kernel<kFeatC, __nv_bfloat16, false><<<(unsigned)ntiles, 128, 0, st>>>(
-        x0, u + cnn_off(0), u + cnn_off(1), A.a1, nullptr, desc, tiles_before, S);
-    conv32_kernel<32, __nv_bfloat16, false><<<(unsigned)ntiles, 128, 0, st>>>(
-        reinterpret_cast<const __nv_bfloat16 *>(A.a1), u + cnn_off(2), u + cnn_off(3), A.a2, nullptr, desc,
-        tiles_before, S);
-    conv32_kernel<32, __nv_bfloat16, false><<<(unsigned)ntiles, 128, 0, st>>>(
-        reinterpret_cast<const __nv_bfloat16 *>(A.a2), u + cnn_off(4), u + cnn_off(5), A.a3, nullptr, desc,
-        tiles_before, S);
+    // the three hidden layers on the tensor cores (conv_tc.cu), the 32 -> 1 layer below
+    __nv_bfloat16 *a1 = reinterpret_cast<__nv_bfloat16 *>(A.a1), *a2 = reinterpret_cast<__nv_bfloat16 *>(A.a2),
+                  *a3 = reinterpret_cast<__nv_bfloat16 *>(A.a3);
+    cudaError_t e = cnn_hidden_tc(0, x0, u + cnn_off(0), u + cnn_off(1), a1, desc, tiles_before, S, ntiles,
+                                  wait_limit_ns, status, st);
+    if (e == cudaSuccess)
+        e = cnn_hidden_tc(1, a1, u + cnn_off(2), u + cnn_off(3), a2, desc, tiles_before, S, ntiles, wait_limit_ns,
+                          status, st);
+    if (e == cudaSuccess)
+        e = cnn_hidden_tc(2, a2, u + cnn_off(4), u + cnn_off(5), a3, desc, tiles_before, S, ntiles, wait_limit_ns,
+                          status, st);
+    if (e != cudaSuccess) return e;
     conv_out_kernel<<<(unsigned)ntiles, kTile, 0, st>>>(reinterpret_cast<const __nv_bfloat16 *>(A.a3),
                                                         u + cnn_off(6), u + cnn_off(7), A.logits, desc, tiles_before, S);
     return cudaGetLastError();

@@ -1,5 +1,8 @@
 // Proposal network: parameter layout, device state and launchers (see cnn.cu).
 #pragma once
+#include <cuda_bf16.h>
+
+#include <algorithm>
 #include <vector>
 
 #include "mt4g_internal.cuh"
@@ -44,8 +47,15 @@ struct CnnActs {
 
 int64_t cnn_tiles(const std::vector<SeriesDesc> &desc, std::vector<int64_t> &tiles_before);
 cudaError_t cnn_prepare(const CnnState &W, cudaStream_t st);
+// Forward pass; wait_limit_ns bounds the tensor-core kernels' waits, whose expiry sets the
+// timeout bit of *status (when not null).
 cudaError_t cnn_forward(const CnnState &W, const uint16_t *feat, const CnnActs &A, const SeriesDesc *desc,
-                        const int64_t *tiles_before, int64_t S, int64_t ntiles, cudaStream_t st);
+                        const int64_t *tiles_before, int64_t S, int64_t ntiles, long long wait_limit_ns,
+                        int32_t *status, cudaStream_t st);
+// One hidden layer (0: 18 -> 32, 1 and 2: 32 -> 32, ReLU, BF16 out) on the tcgen05 tensor cores.
+cudaError_t cnn_hidden_tc(int layer, const __nv_bfloat16 *in, const float *W, const float *bias, __nv_bfloat16 *out,
+                          const SeriesDesc *desc, const int64_t *tiles_before, int64_t S, int64_t ntiles,
+                          long long wait_limit_ns, int32_t *status, cudaStream_t st);
 cudaError_t cnn_backward(const CnnState &W, const uint16_t *feat, const CnnActs &A, const int32_t *cp_count,
                          const int32_t *cp_idx, int32_t max_cp, const SeriesDesc *desc, int64_t S, int T,
                          float *grad, float *loss, cudaStream_t st);
