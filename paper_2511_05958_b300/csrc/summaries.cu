@@ -12,7 +12,7 @@
 //
 // One warp per step: the step's m <= 256 samples are sorted in registers by a bitonic
 // network (V values per lane, partners across lanes by shuffle), then lanes 0..15 pick
-// their quantile.
+// their quantile.  Each warp takes every eighth step and loads the next one while sorting.
 #include <cuda_bf16.h>
 
 #include "mt4g_internal.cuh"
@@ -60,31 +60,43 @@ __device__ __forceinline__ void bitonic_sort_warp(uint32_t (&x)[V]) {
     }
 }
 
+// Features of steps warp, warp + 8, ... of one series; each step's samples are loaded one
+// step ahead, so the loads of the next step are in flight while this one is sorted.
 template <int V>
-__device__ void summarise_step(const uint32_t *__restrict__ row, int m, float lmed, int t,
-                               __nv_bfloat16 *__restrict__ out) {
+__device__ void summarise_steps(const uint32_t *__restrict__ x0, int T, int m, float lmed, int warp,
+                                __nv_bfloat16 *__restrict__ base) {
     const int lane = threadIdx.x & 31;
-    uint32_t x[V];
+    uint32_t nx[V];
+    auto load = [&](int t, uint32_t(&v)[V]) {
+        const uint32_t *row = x0 + (int64_t)t * m;
 #pragma unroll
-    for (int r = 0; r < V; r++) {
-        const int e = lane * V + r;
-        x[r] = e < m ? __ldg(row + e) : 0xffffffffu;
-    }
-    bitonic_sort_warp<V>(x);
+        for (int r = 0; r < V; r++) {
+            const int e = lane * V + r;
+            v[r] = e < m ? __ldg(row + e) : 0xffffffffu;
+        }
+    };
+    if (warp < T) load(warp, nx);
     const int i = lane & 15;
     const int rank = min(m - 1, ((2 * i + 1) * m) / 32);
-    uint32_t q = 0;
+    for (int t = warp; t < T; t += 8) {
+        uint32_t x[V];
 #pragma unroll
-    for (int r = 0; r < V; r++) {
-        const uint32_t v = __shfl_sync(kFull, x[r], rank / V);
-        if (rank % V == r) q = v;
+        for (int r = 0; r < V; r++) x[r] = nx[r];
+        if (t + 8 < T) load(t + 8, nx);
+        bitonic_sort_warp<V>(x);
+        uint32_t q = 0;
+#pragma unroll
+        for (int r = 0; r < V; r++) {
+            const uint32_t v = __shfl_sync(kFull, x[r], rank / V);
+            if (rank % V == r) q = v;
+        }
+        float f = 0.f;
+        if (lane < 16)
+            f = log2f((float)max(q, 1u)) - lmed;
+        else if (lane == 16)
+            f = log2f(1024.f + 32.f * (float)t) - 10.f;
+        if (lane < kFeatC) base[(int64_t)(2 + t) * kFeatC + lane] = __float2bfloat16_rn(f);
     }
-    float f = 0.f;
-    if (lane < 16)
-        f = log2f((float)max(q, 1u)) - lmed;
-    else if (lane == 16)
-        f = log2f(1024.f + 32.f * (float)t) - 10.f;
-    if (lane < kFeatC) out[lane] = __float2bfloat16_rn(f);
 }
 
 __global__ void __launch_bounds__(256, 4) summaries_kernel(const uint32_t *__restrict__ samples,
@@ -102,18 +114,15 @@ __global__ void __launch_bounds__(256, 4) summaries_kernel(const uint32_t *__res
             base[(int64_t)(d.T + 2) * kFeatC + c] = __float2bfloat16_rn(0.f);
         }
     }
-    for (int t = warp; t < d.T; t += 8) {
-        const uint32_t *row = samples + d.off + (int64_t)t * d.m;
-        __nv_bfloat16 *out = base + (int64_t)(2 + t) * kFeatC;
-        if (d.m <= 32)
-            summarise_step<1>(row, d.m, lmed, t, out);
-        else if (d.m <= 64)
-            summarise_step<2>(row, d.m, lmed, t, out);
-        else if (d.m <= 128)
-            summarise_step<4>(row, d.m, lmed, t, out);
-        else
-            summarise_step<8>(row, d.m, lmed, t, out);
-    }
+    const uint32_t *x0 = samples + d.off;
+    if (d.m <= 32)
+        summarise_steps<1>(x0, d.T, d.m, lmed, warp, base);
+    else if (d.m <= 64)
+        summarise_steps<2>(x0, d.T, d.m, lmed, warp, base);
+    else if (d.m <= 128)
+        summarise_steps<4>(x0, d.T, d.m, lmed, warp, base);
+    else
+        summarise_steps<8>(x0, d.T, d.m, lmed, warp, base);
 }
 
 }  // namespace
