@@ -49,9 +49,11 @@ WORKLOADS = {
 LAUNCHES = {False: 4, True: 14}  # our kernels per call (plain / learned)
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch, per series, from the ncu
 # captures summarised in profiles/ (queue_kernel_plain_1024x512x128.md,
-# sort_series_kernel_1024x512x128.md); keyed by (workload, stage).  Only workloads whose kernels
-# were captured as they are now appear here; the others report null.
-NCU_TRAFFIC_PER_SERIES = {("plain", "queue"): 540.076288e6 / 1024, ("plain", "sort"): 1306.98496e6 / 1024}
+# sort_series_kernel_1024x512x128.md, queue_kernel_learned_2048x512x128.md); keyed by (workload,
+# stage) and scaled by the number of series (the learned capture has 2048 of the 65,536 series).
+# Only workloads whose kernels were captured as they are now appear here; the others report null.
+NCU_TRAFFIC_PER_SERIES = {("plain", "queue"): 539.373312e6 / 1024, ("plain", "sort"): 1306.65088e6 / 1024,
+                          ("learned", "queue"): 2065.306e6 / 2048}
 STAGES = ["upload", "sort", "proposals", "queue", "collect"]
 
 
