@@ -47,6 +47,8 @@ WORKLOADS = {
     "uneven": (3, 2, 16384, False, "plain full segmentation, 16384 uneven series, T 32..4096, m 8..256"),
 }
 LAUNCHES = {False: 4, True: 14}  # our kernels per call (plain / learned)
+RECIPES = {2: "synth recipe 2 (T=512, m=128, levels 35/300/800/1100, 0.5% outliers)",
+           3: "synth recipe 3 (T 32..4096, m 8..256, 0-4 level ratios 1.01..30, Pareto tails)"}
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch, per series, from the ncu
 # captures summarised in profiles/ (queue_kernel_plain_1024x512x128.md,
 # sort_series_kernel_1024x512x128.md, queue_kernel_learned_2048x512x128.md); keyed by (workload,
@@ -79,7 +81,7 @@ def dist_info():
 def workload_config(name, world, S):
     cfg, seed, _, learned, desc = WORKLOADS[name]
     return {"workload": desc, "series_per_gpu": S, "global_series": S * world, "alpha": ALPHA, "min_seg": 1,
-            "max_cp": MAX_CP, "generator": f"config {cfg}, seed {seed}", "learned": learned,
+            "max_cp": MAX_CP, "generator": f"{RECIPES[cfg]}, seed {seed}", "learned": learned,
             "l2": "inputs larger than L2", "parallelism": f"replicas x{world} (series sharded, no collective)"}
 
 

@@ -159,7 +159,7 @@ int mt4g_ks_segment_host(mt4g_ctx *ctx, const uint32_t *samples_host, const int6
  * The paper scans every index (Sec. IV-B-1 (4)) and notes that candidate change points
  * can be shortlisted first to save computation, a step MT4G omits because its datasets
  * are small (Sec. IV-B-1, after step (4)).  The calls below build such a shortlist with a
- * small 1D CNN over per-step summaries; the exact scan stays the judge of every answer.
+ * small 1D CNN over per-step summaries; the exact scan still decides every answer.
  *
  * Features (mt4g_summaries): for each step t of a series, 17 values
  *   i < 16: log2(q_i) - log2(med), q_i = the step's sorted sample at rank

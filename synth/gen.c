@@ -27,7 +27,7 @@
  *      medians 35, 300, 800, 1100 with lognormal sigma .05, .05, .08, .10;
  *      each sample replaced w.p. 0.005 by U{2000..10000}.
  *   3  T ~ U{32..4096}, m ~ U{8,16,64,256}, #cp ~ U{0..4} clipped to
- *      floor(T/16)-1, placed as in cfg 2 with minimum segment 16; base median
+ *      floor(T/16)-1, placed as in workload 2 with minimum segment 16; base median
  *      35, each next median multiplied by r, r log-uniform in [1.01, 30];
  *      sigma .05; each sample replaced w.p. 0.01 by a Pareto(1.5) draw with
  *      x_m = the level median.

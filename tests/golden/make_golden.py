@@ -30,7 +30,7 @@ def main():
                                "num": cnum[0, :cnt[0]].tolist(), "den": cden[0, :cnt[0]].tolist(),
                                "p": cp[0, :cnt[0]].tolist()},
     }
-    with open(os.path.join(HERE, "config1_oracle.json"), "w") as f:
+    with open(os.path.join(HERE, "single_series_64x32_oracle.json"), "w") as f:
         json.dump(out, f, indent=1)
         f.write("\n")
 

@@ -227,7 +227,7 @@ def _assert_same(full, learned):
 
 
 @pytest.mark.parametrize("seed", [0, 1])
-def test_learned_mode_equals_full_on_config2(eng, seed):
+def test_learned_mode_equals_full_on_three_level_series(eng, seed):
     import oracle
     b = synth.generate(2, 20 + seed, 256)
     eng.cnn_init(100 + seed)  # untrained: windows are often wrong, certification must catch it
@@ -282,7 +282,7 @@ def test_learned_mode_random_shapes_and_min_seg(eng):
         eng.set_option(mt4g.OPT_CONF_MIN_PPM, 900000)
 
 
-def test_learned_mode_uneven_config3_sample(eng):
+def test_learned_mode_uneven_sample(eng):
     b3 = synth.generate(3, 2, 400)
     keep = [s for s in range(400) if b3.m[s] <= 256 and float(b3.steps[s]) ** 2 * float(b3.m[s]) < 4e8][:120]
     b = synth.from_arrays([b3.series(s) for s in keep])

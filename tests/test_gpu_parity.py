@@ -66,18 +66,18 @@ def check_segment(eng, b, alpha, min_seg=1, max_cp=16, mode=mt4g.MODE_FULL, nthr
 
 # ------------------------------------------------------------------ small exact cases
 
-def test_config1_scan_matches_oracle_and_golden(eng):
+def test_single_series_64x32_scan_matches_oracle_and_golden(eng):
     import json
     import os
     b = synth.generate(1, 0, 1)
     check_scan(eng, b)
     k, num, den, p = gpu_scan(eng, b)
-    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "config1_oracle.json")))
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "single_series_64x32_oracle.json")))
     assert (int(k[0]), int(num[0]), int(den[0]), float(p[0])) == \
         (g["scan"]["k"], g["scan"]["num"], g["scan"]["den"], g["scan"]["p"])
 
 
-def test_config1_segment(eng):
+def test_single_series_64x32_segment(eng):
     b = synth.generate(1, 0, 1)
     cnt, idx = check_segment(eng, b, 1e-6)
     assert cnt[0] == 1 and idx[0, 0] == 40
@@ -229,7 +229,7 @@ def test_repeated_calls_reuse_workspace(eng):
 
 # ------------------------------------------------------------------ full-size workloads, sampled
 
-def test_config2_full_batch_sampled(eng):
+def test_three_level_1024x512x128_batch_sampled(eng):
     """1024 series, T=512, m=128: the whole batch on the GPU, the oracle on 48 sampled series."""
     b = synth.generate(2, 1, 1024)
     rc, cnt, idx, num, den, p = gpu_segment(eng, b, 1e-6, 1, 16)
@@ -251,7 +251,7 @@ def test_config2_full_batch_sampled(eng):
     assert truth >= 0.95 * 1024
 
 
-def test_config3_uneven_batch_sampled(eng):
+def test_uneven_16384_batch_sampled(eng):
     """16384 uneven series (T 32..4096, m 8..256): the full batch on the GPU; the oracle on the
     sampled series it finishes quickly; structural properties on all."""
     b = synth.generate(3, 2, 16384)

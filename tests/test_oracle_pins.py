@@ -322,13 +322,13 @@ def test_segmentation_capacity_reports_true_count():
     assert np.array_equal(idx[0], idx_full[0, :4])
 
 
-def test_config1_recovers_truth():
+def test_single_series_64x32_recovers_truth():
     b = synth.generate(1, 0, 1)
     k, num, den, p = oracle.ks_scan(b.samples, b.offsets, b.steps)
     assert k[0] == 40 and p[0] == 0.0 and num[0] <= den[0] and num[0] / den[0] > 0.98
 
 
-def test_config2_truth_recovery_is_high():
+def test_three_level_truth_recovery_is_high():
     """Sanity statistic only: the exact segmentation finds the generator's change points."""
     b = synth.generate(2, 1, 8)
     rc, cnt, idx, *_ = oracle.ks_segment(b.samples, b.offsets, b.steps, 1e-6, nthreads=8)
@@ -355,11 +355,11 @@ def test_reduce_series_values():
     assert np.allclose(S, [math.sqrt(5), 0.0, math.sqrt(65)], rtol=0, atol=1e-15)
 
 
-def test_config1_golden_fixture():
+def test_single_series_64x32_golden_fixture():
     """The stored fixture (written by tests/golden/make_golden.py from the oracle) still holds."""
     import json
     import os
-    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "config1_oracle.json")))
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "single_series_64x32_oracle.json")))
     b = synth.generate(1, 0, 1)
     assert int(b.samples.astype(np.uint64).sum()) == g["samples_sum"]
     k, num, den, p = oracle.ks_scan(b.samples, b.offsets, b.steps)
