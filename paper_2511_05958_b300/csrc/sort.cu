@@ -69,12 +69,18 @@ __device__ __forceinline__ unsigned digit_peers(uint32_t dg, unsigned vm) {
     return peers;
 }
 
-// Warp-aggregated shared-memory histogram increment.  Every lane calls it; lanes outside
-// vm contribute nothing.
+// Shared-memory histogram increment.  Every lane calls it; lanes outside vm contribute
+// nothing.  Digits of a narrow range are aggregated per warp by match.any (one atomic per
+// distinct digit); digits of a wide range rarely collide, so each lane adds its own.
 __device__ __forceinline__ void hist_add(uint32_t *h, uint32_t dg, unsigned vm) {
-    const unsigned peers = digit_peers(dg, vm);
     const bool valid = (vm >> (threadIdx.x & 31)) & 1u;
-    if (valid && (int)(__ffs(peers) - 1) == (int)(threadIdx.x & 31)) atomicAdd(h + dg, (uint32_t)__popc(peers));
+    const uint32_t dmin = __reduce_min_sync(kFull, dg), dmax = __reduce_max_sync(kFull, dg);
+    if (dmax - dmin < 12u) {
+        const unsigned peers = __match_any_sync(kFull, dg) & vm;
+        if (valid && (int)(__ffs(peers) - 1) == (int)(threadIdx.x & 31)) atomicAdd(h + dg, (uint32_t)__popc(peers));
+    } else if (valid) {
+        atomicAdd(h + dg, 1u);
+    }
 }
 
 // e / m for 0 <= e < 2^30 by a single-precision reciprocal and an exact correction.
@@ -233,13 +239,21 @@ sort_series_kernel(const uint32_t *__restrict__ samples, SeriesDesc *__restrict_
     if (tid < 256) sm.hist[tid] = 0;
     __syncthreads();
     uint32_t vmax = 0;
-    for (int b0 = 0; b0 < N; b0 += kSortThreads) {
-        const int i = b0 + tid;
-        const bool valid = i < N;
-        const unsigned vm = __ballot_sync(kFull, valid);
-        const uint32_t v = valid ? __ldg(in + i) : 0u;
-        vmax = max(vmax, v);
-        hist_add(sm.hist, v & 255u, vm);
+    for (int b0 = 0; b0 < N; b0 += kSortThreads * kSortItems) {
+        // all loads of the round first, so they are in flight together
+        uint32_t v[kSortItems];
+#pragma unroll
+        for (int it = 0; it < kSortItems; it++) {
+            const int i = b0 + it * kSortThreads + tid;
+            v[it] = i < N ? __ldg(in + i) : 0u;
+        }
+#pragma unroll
+        for (int it = 0; it < kSortItems; it++) {
+            const int i = b0 + it * kSortThreads + tid;
+            const unsigned vm = __ballot_sync(kFull, i < N);
+            vmax = max(vmax, v[it]);
+            hist_add(sm.hist, v[it] & 255u, vm);
+        }
     }
     vmax = __reduce_max_sync(kFull, vmax);
     if (lane == 0) sm.tmp[warp] = vmax;
