@@ -215,13 +215,26 @@ __device__ void scan_slice1(const uint16_t *__restrict__ lab, const int32_t *__r
     nonempty = 0;
     ws.hist[lane] = 0;
     __syncwarp();
+    // the run bounds and end labels of the next batch are loaded one batch ahead: the run
+    // bounds before this batch's staging, the end labels before its walk
+    int na0 = 0, nb0 = 0, nf0 = 0, nl0 = 0;
+    if (lane < U) {
+        na0 = __ldg(rt + lane);
+        nb0 = __ldg(rt + lane + 1);
+        nf0 = __ldg(lab + na0);
+        nl0 = __ldg(lab + nb0 - 1);
+    }
     for (int j0 = 0; j0 < U; j0 += 32) {
         const int j = j0 + lane;
         int si = 0, ei = 0, c0 = 0, n_av = 0, L = 0;
         bool la_lt = false;
+        const int a0 = na0, b0 = nb0, f0 = nf0, l0 = nl0;
+        const int jn = j + 32;
+        if (jn < U) {
+            na0 = __ldg(rt + jn);
+            nb0 = __ldg(rt + jn + 1);
+        }
         if (j < U) {
-            const int a0 = __ldg(rt + j), b0 = __ldg(rt + j + 1);
-            const int f0 = __ldg(lab + a0), l0 = __ldg(lab + b0 - 1);
             si = (f0 >= lo) ? a0 : (l0 < lo ? b0 : lower_bound_lab(lab, a0, b0, lo));
             ei = (l0 < hi) ? b0 : (f0 >= hi ? a0 : lower_bound_lab(lab, si, b0, hi));
             if (ei > si) {
@@ -285,6 +298,10 @@ __device__ void scan_slice1(const uint16_t *__restrict__ lab, const int32_t *__r
         }
         spec = __reduce_or_sync(kFull, spec);
         const int cbt = __shfl_sync(kFull, cbs, 31), nt = __shfl_sync(kFull, ns, 31);
+        if (jn < U) {
+            nf0 = __ldg(lab + na0);
+            nl0 = __ldg(lab + nb0 - 1);
+        }
         __syncwarp();
         const int cnt = __popc(ne);
         int r = 0;
@@ -463,12 +480,24 @@ __device__ __noinline__ void scan_grid(const uint16_t *__restrict__ lab, const i
     int64_t cl = 0, C = 0;
     uint64_t mx = 0, ub = 0;
     nonempty = 0;
+    // run bounds and end labels of the next batch are loaded one batch ahead (as in scan_slice1)
+    int na0 = 0, nb0 = 0, nf0 = 0, nl0 = 0;
+    if (lane < U) {
+        na0 = __ldg(rt + lane);
+        nb0 = __ldg(rt + lane + 1);
+        nf0 = __ldg(lab + na0);
+        nl0 = __ldg(lab + nb0 - 1);
+    }
     for (int j0 = 0; j0 < U; j0 += 32) {
         const int j = j0 + lane;
         int si = 0, ei = 0, fi = 0, la = 0;
+        const int a0 = na0, b0 = nb0, f0 = nf0, l0 = nl0;
+        const int jn = j + 32;
+        if (jn < U) {
+            na0 = __ldg(rt + jn);
+            nb0 = __ldg(rt + jn + 1);
+        }
         if (j < U) {
-            const int a0 = __ldg(rt + j), b0 = __ldg(rt + j + 1);
-            const int f0 = __ldg(lab + a0), l0 = __ldg(lab + b0 - 1);
             si = (f0 >= lo) ? a0 : (l0 < lo ? b0 : lower_bound_lab(lab, a0, b0, lo));
             ei = (l0 < hi) ? b0 : (f0 >= hi ? a0 : lower_bound_lab(lab, si, b0, hi));
             if (ei > si) {
@@ -483,6 +512,10 @@ __device__ __noinline__ void scan_grid(const uint16_t *__restrict__ lab, const i
             st.ei[pos] = ei;
             st.cb[0][pos] = fi;
             st.cb[1][pos] = la;
+        }
+        if (jn < U) {
+            nf0 = __ldg(lab + na0);
+            nl0 = __ldg(lab + nb0 - 1);
         }
         __syncwarp();
         const int cnt = __popc(ne);
