@@ -297,3 +297,11 @@ def test_latency_stats_match_oracle(eng):
     assert np.array_equal(p50.view(np.uint32), o50) and np.array_equal(p95.view(np.uint32), o95)
     assert np.array_equal(mean, om), np.nonzero(mean != om)
     assert np.array_equal(std, ostd), np.nonzero(std != ostd)
+
+
+def test_int32_peak_is_a_plausible_rate():
+    """mt4g_int32_peak: the scan's 4-op integer mix on every SM, in 10^12 ops/s.  B300 has 148 SMs x
+    128 integer lanes at up to 2.032 GHz (38.5 Tops/s); a working measurement lands below that and
+    well above a tenth of it."""
+    v = mt4g.int32_peak(0)
+    assert 3.0 < v < 40.0, v
