@@ -146,10 +146,14 @@ __device__ void lsd_passes(SortSmem &sm, int passes, const uint32_t *__restrict_
                 }
             }
             if (p == 0) {
+                // step label = sample index / m (a shift when m is a power of two, as it usually is)
+                const bool pow2 = (m & (m - 1)) == 0;
+                const int msh = __ffs(m) - 1;
 #pragma unroll
                 for (int it = 0; it < kSortItems; it++) {
                     const int e = tb + warp * (32 * kSortItems) + it * 32 + lane;
-                    const uint32_t t = div_step((uint32_t)min(e, N - 1), (uint32_t)m, inv_m);
+                    const uint32_t ec = (uint32_t)min(e, N - 1);
+                    const uint32_t t = pow2 ? ec >> msh : div_step(ec, (uint32_t)m, inv_m);
                     if (COMP) key[it] = (key[it] << 16) | t;
                     lb[it] = (uint16_t)t;
                 }
