@@ -340,6 +340,12 @@ def main():
         t = run_oracle(sb, cores)
         line["cpu_baseline"] = {"value": sb.S / t, "unit": "series/s", "cores": cores, "kind": "oracle",
                                 "sample": f"{desc}, one segmentation pass, {t:.1f} s"}
+        # the same oracle on one host thread, on the first 64 series of that sample
+        import synth
+        one = synth.from_arrays([sb.series(s) for s in range(min(64, sb.S))])
+        t1 = run_oracle(one, 1)
+        line["cpu_baseline"]["single_thread"] = {"value": one.S / t1, "unit": "series/s", "cores": 1,
+                                                 "sample": f"first {one.S} series of the sample, {t1:.1f} s"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     eng.close()
