@@ -12,6 +12,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "mt4g_cnn.cuh"
 
 using namespace mt4g;
@@ -82,6 +84,14 @@ struct mt4g_ctx {
     uint32_t call_counter = 0;
     size_t ready_off = (size_t)-1;
     unsigned long long ready_cap = 0;
+};
+
+// NVTX range over an entry point's host-side work (header-only NVTX 3: free without a tool).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
 namespace {
@@ -842,6 +852,7 @@ extern "C" {
 int mt4g_ks_scan(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets, const int32_t *steps, int64_t S,
                  int32_t mode, int32_t *k_out, int64_t *dnum_out, int64_t *dden_out, double *p_out,
                  void *cuda_stream) {
+    NvtxRange nvtx("mt4g_ks_scan");
     int rc = begin_call(ctx);
     if (rc) return rc;
     if (mode == MT4G_MODE_LEARNED) return fail(ctx, MT4G_EINVAL, "mt4g_ks_scan has no learned mode");
@@ -860,6 +871,7 @@ int mt4g_ks_scan(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets,
 int mt4g_ks_segment(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets, const int32_t *steps, int64_t S,
                     double alpha, int32_t min_seg, int32_t max_cp, int32_t mode, int32_t *cp_count, int32_t *cp_idx,
                     int64_t *dnum, int64_t *dden, double *p, int32_t *fallback, void *cuda_stream) {
+    NvtxRange nvtx("mt4g_ks_segment");
     int rc = begin_call(ctx);
     if (rc) return rc;
     const void *outs[6] = {cp_count, cp_idx, dnum, dden, p, fallback};
@@ -879,6 +891,7 @@ int mt4g_ks_segment_host(mt4g_ctx *ctx, const uint32_t *samples_host, const int6
                          int64_t S, double alpha, int32_t min_seg, int32_t max_cp, int32_t mode,
                          int64_t chunk_samples, int32_t *cp_count, int32_t *cp_idx, int64_t *dnum, int64_t *dden,
                          double *p, int32_t *fallback, void *cuda_stream) {
+    NvtxRange nvtx("mt4g_ks_segment_host");
     int rc = begin_call(ctx);
     if (rc) return rc;
     if (S < 0 || (S > 0 && (!offsets || !steps))) return fail(ctx, MT4G_EINVAL, "bad host tables");
@@ -936,6 +949,7 @@ int mt4g_ks_segment_host(mt4g_ctx *ctx, const uint32_t *samples_host, const int6
     for (int b = 0; b < 2; b++) CUDA_TRY(ctx, cudaEventRecord(ctx->ev_free[b], st));
     std::vector<int64_t> loc;
     for (int64_t c = 0; c < nchunks; c++) {
+        NvtxRange chunk_range("mt4g_ks_segment_host chunk");
         const int b = (int)(c & 1);
         const int64_t s0 = first[c], n = first[c + 1] - first[c];
         const int64_t base = offsets[s0], cnt = offsets[first[c + 1]] - base;
@@ -1260,6 +1274,7 @@ int mt4g_cnn_load(mt4g_ctx *c, const char *path) {
 
 int mt4g_summaries(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets, const int32_t *steps, int64_t S,
                    uint16_t *feat_out, void *cuda_stream) {
+    NvtxRange nvtx("mt4g_summaries");
     int rc = begin_call(ctx);
     if (rc) return rc;
     if (S > 0 && (!samples || !feat_out)) return fail(ctx, MT4G_EINVAL, "NULL device pointer");
@@ -1284,6 +1299,7 @@ int mt4g_summaries(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offset
 int mt4g_latency_stats(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets, const int32_t *steps,
                        int64_t S, double *mean_out, uint32_t *p50_out, uint32_t *p95_out, double *std_out,
                        void *cuda_stream) {
+    NvtxRange nvtx("mt4g_latency_stats");
     int rc = begin_call(ctx);
     if (rc) return rc;
     if (S > 0 && (!samples || !mean_out || !p50_out || !p95_out || !std_out))
@@ -1306,6 +1322,7 @@ int mt4g_latency_stats(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *of
 
 int mt4g_cnn_forward(mt4g_ctx *c, const uint16_t *feat, const int32_t *steps, int64_t S, float *logits_out,
                      void *cuda_stream) {
+    NvtxRange nvtx("mt4g_cnn_forward");
     int rc = begin_call(c);
     if (rc) return rc;
     if (!c->cnn_ready) return fail(c, MT4G_EINVAL, "no weights: call mt4g_cnn_init or mt4g_cnn_load");
@@ -1365,6 +1382,7 @@ static int cnn_fwd_bwd(mt4g_ctx *c, const uint16_t *feat, int32_t T, int64_t Bn,
 
 int mt4g_cnn_grads(mt4g_ctx *c, const uint16_t *feat, int32_t T, int64_t B, const int32_t *cp_count,
                    const int32_t *cp_idx, int32_t max_cp, float *grad_out, float *loss_out, void *cuda_stream) {
+    NvtxRange nvtx("mt4g_cnn_grads");
     int rc = begin_call(c);
     if (rc) return rc;
     if (!grad_out) return fail(c, MT4G_EINVAL, "NULL gradient buffer");
@@ -1373,6 +1391,7 @@ int mt4g_cnn_grads(mt4g_ctx *c, const uint16_t *feat, int32_t T, int64_t B, cons
 
 int mt4g_cnn_train_step(mt4g_ctx *c, const uint16_t *feat, int32_t T, int64_t B, const int32_t *cp_count,
                         const int32_t *cp_idx, int32_t max_cp, float lr, float *loss_out, void *cuda_stream) {
+    NvtxRange nvtx("mt4g_cnn_train_step");
     int rc = begin_call(c);
     if (rc) return rc;
     if (!(lr > 0.f)) return fail(c, MT4G_EINVAL, "learning rate must be > 0");
@@ -1386,6 +1405,7 @@ int mt4g_cnn_train_step(mt4g_ctx *c, const uint16_t *feat, int32_t T, int64_t B,
 
 int mt4g_propose(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets, const int32_t *steps, int64_t S,
                  int32_t n_win, int32_t half_width, int32_t *win_center, float *conf, void *cuda_stream) {
+    NvtxRange nvtx("mt4g_propose");
     int rc = begin_call(ctx);
     if (rc) return rc;
     if (!ctx->cnn_ready) return fail(ctx, MT4G_EINVAL, "no weights: call mt4g_cnn_init or mt4g_cnn_load");

@@ -2,6 +2,7 @@
 
     python -m paper_2511_05958_b300.train [--series 2000000] [--steps 20000] [--batch 512]
                                           [--lr 1e-3] [--seed 3] [--out weights/cnn_c2.bin]
+                                          [--checkpoint-every N] [--resume]
 
 Training set: `series` series of the T=512, m=128, three-change-point workload (lognormal levels
 35/300/800/1100 cycles, 0.5% outliers; generator seed 3), drawn on the GPU in chunks.  Each chunk
@@ -10,7 +11,9 @@ targets) and summarised (17 features per step); the raw samples are then dropped
 costs about 18.6 KB per series on the device.  Training: `steps` Adam steps (lr, beta 0.9/0.999,
 eps 1e-8) on batches of `batch` series drawn uniformly with replacement.  The weights file and a
 JSON log (loss curve, label statistics, timings, and the proposal quality on a held-out batch)
-are written beside each other.
+are written beside each other.  With --checkpoint-every N the weights and Adam state (the
+library's checksummed format) are also written every N steps to OUT.ckpt, with the step in
+OUT.ckpt.json; --resume continues from there.
 """
 from __future__ import annotations
 
@@ -86,6 +89,11 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=3)
     ap.add_argument("--init-seed", type=int, default=12345)
     ap.add_argument("--out", default=os.path.join(HERE, "weights", "cnn_c2.bin"))
+    ap.add_argument("--checkpoint-every", type=int, default=0,
+                    help="every N steps write weights + Adam state to OUT.ckpt (0: only the final file)")
+    ap.add_argument("--eval-series", type=int, default=2048, help="held-out series for the proposal quality")
+    ap.add_argument("--resume", action="store_true",
+                    help="continue from OUT.ckpt (weights, Adam moments and step) instead of a fresh init")
     args = ap.parse_args(argv)
 
     import torch
@@ -104,14 +112,24 @@ def main(argv=None):
     log["labels"] = {"mean_cps": float(c.mean()), "frac_3_cps": float(np.mean(c == 3)),
                      "frac_0_cps": float(np.mean(c == 0)), "exact_truth_recovery": hits / args.series}
 
-    eng.cnn_init(args.init_seed)
+    ckpt = args.out + ".ckpt"
+    first_step = 1
+    if args.resume and os.path.exists(ckpt):
+        # the checkpoint carries the weights, the Adam moments and the Adam step; its sidecar the
+        # loop step.  Batches after a resume are drawn from a generator reseeded with that step.
+        eng.cnn_load(ckpt)
+        with open(ckpt + ".json") as f:
+            first_step = int(json.load(f)["step"]) + 1
+        log["resumed_at_step"] = first_step - 1
+    else:
+        eng.cnn_init(args.init_seed)
     g = torch.Generator(device=dev)
-    g.manual_seed(args.seed)
+    g.manual_seed(args.seed + (first_step - 1))
     loss = torch.zeros(1, dtype=torch.float32, device=dev)
     curve = []
     t1 = time.time()
     acc, nacc = 0.0, 0
-    for step in range(1, args.steps + 1):
+    for step in range(first_step, args.steps + 1):
         sel = torch.randint(0, args.series, (args.batch,), device=dev, generator=g)
         bf = feats.index_select(0, sel).view(-1, mt4g.FEAT_CHANNELS)
         eng.cnn_train_step(bf, T_STEPS, args.batch, cnt.index_select(0, sel), idx.index_select(0, sel).contiguous(),
@@ -123,12 +141,17 @@ def main(argv=None):
             curve.append({"step": step, "loss": acc / max(nacc, 1)})
             print(f"step {step}: loss {acc / max(nacc, 1):.4f}", flush=True)
             acc, nacc = 0.0, 0
+        if args.checkpoint_every and step % args.checkpoint_every == 0:
+            os.makedirs(os.path.dirname(os.path.abspath(ckpt)), exist_ok=True)
+            eng.cnn_save(ckpt)
+            with open(ckpt + ".json", "w") as f:
+                json.dump({"step": step}, f)
     torch.cuda.synchronize()
     log["train_seconds"] = time.time() - t1
     log["loss_curve"] = curve
     os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
     eng.cnn_save(args.out)
-    log["held_out"] = evaluate(eng, 4, 2048, dev)
+    log["held_out"] = evaluate(eng, 4, args.eval_series, dev)
     with open(os.path.splitext(args.out)[0] + ".train.json", "w") as f:
         json.dump(log, f, indent=1)
         f.write("\n")

@@ -345,3 +345,27 @@ def test_trained_network_gains_over_untrained():
     assert tr["covered"] >= 0.95 and un["covered"] < 0.5, msg
     assert tr["conf"] >= 0.9 > un["conf"], msg
     assert tr["evals"] < un["evals"] < evals_full * 1.5, msg
+
+
+def test_training_checkpoint_and_resume(tmp_path):
+    """train.py writes the weights and Adam state every N steps and continues from them."""
+    import json
+    import os
+    from paper_2511_05958_b300 import train
+    out = str(tmp_path / "w.bin")
+    common = ["--series", "256", "--chunk", "128", "--batch", "32", "--eval-series", "64", "--out", out]
+    train.main(common + ["--steps", "20", "--checkpoint-every", "10"])
+    assert os.path.exists(out + ".ckpt") and json.load(open(out + ".ckpt.json"))["step"] == 20
+    e = mt4g.Engine(0)
+    e.cnn_load(out + ".ckpt")
+    w20 = e.cnn_get_params()
+    e.close()
+    train.main(common + ["--steps", "30", "--checkpoint-every", "10", "--resume"])
+    log = json.load(open(os.path.splitext(out)[0] + ".train.json"))
+    assert log["resumed_at_step"] == 20 and log["loss_curve"][-1]["step"] == 30
+    e = mt4g.Engine(0)
+    e.cnn_load(out)
+    w30 = e.cnn_get_params()
+    e.close()
+    assert np.isfinite(w30).all() and not np.array_equal(w20, w30)
+    assert json.load(open(out + ".ckpt.json"))["step"] == 30
