@@ -898,8 +898,27 @@ int mt4g_ks_segment_host(mt4g_ctx *ctx, const uint32_t *samples_host, const int6
     if (S == 0) return MT4G_OK;
     if (!samples_host) return fail(ctx, MT4G_EINVAL, "NULL host sample pointer");
     if (offsets[0] != 0) return fail(ctx, MT4G_EINVAL, "offsets[0] must be 0");
-    for (int64_t s = 0; s < S; s++)
-        if (offsets[s + 1] < offsets[s]) return fail(ctx, MT4G_EINVAL, "offsets must be non-decreasing");
+    // everything a chunk's segmentation would reject, checked before any chunk is enqueued
+    if (!(alpha > 0.0 && alpha < 1.0)) return fail(ctx, MT4G_EINVAL, "alpha must be in (0, 1)");
+    if (max_cp < 0) return fail(ctx, MT4G_EINVAL, "max_cp must be >= 0");
+    if (min_seg < 1) return fail(ctx, MT4G_EINVAL, "min_seg must be >= 1 (got %d)", min_seg);
+    if (mode != MT4G_MODE_FULL && mode != MT4G_MODE_REDUCED && mode != MT4G_MODE_LEARNED)
+        return fail(ctx, MT4G_EINVAL, "mode must be MT4G_MODE_FULL, _REDUCED or _LEARNED (got %d)", mode);
+    if (mode == MT4G_MODE_LEARNED && !ctx->cnn_ready)
+        return fail(ctx, MT4G_EINVAL, "learned mode needs weights: call mt4g_cnn_load or mt4g_cnn_init");
+    if (!cp_count || (max_cp > 0 && (!cp_idx || !dnum || !dden || !p)))
+        return fail(ctx, MT4G_EINVAL, "NULL device pointer");
+    for (int64_t s = 0; s < S; s++) {
+        const int64_t n = offsets[s + 1] - offsets[s];
+        const int32_t T = steps[s];
+        if (T < 2 || T > MT4G_MAX_STEPS)
+            return fail(ctx, MT4G_EINVAL, "series %lld: T=%d outside [2, %d]", (long long)s, T, MT4G_MAX_STEPS);
+        if (n <= 0 || n % T != 0 || n > MT4G_MAX_SERIES_SAMPLES)
+            return fail(ctx, MT4G_EINVAL, "series %lld: %lld samples is not a positive multiple of T=%d within %lld",
+                        (long long)s, (long long)n, T, (long long)MT4G_MAX_SERIES_SAMPLES);
+        if (mode == MT4G_MODE_LEARNED && n / T > 256)
+            return fail(ctx, MT4G_EINVAL, "series %lld: learned mode needs m <= 256", (long long)s);
+    }
     // default: about eight chunks (the first copy and the last chunk's work are not overlapped;
     // much smaller chunks leave the GPU underused), none below 2^24 samples
     if (chunk_samples <= 0) chunk_samples = std::max<int64_t>((int64_t)1 << 24, (offsets[S] + 7) / 8);

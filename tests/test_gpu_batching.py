@@ -128,3 +128,16 @@ def test_host_input_chunks_match_device_input(eng):
             assert np.array_equal(a.cpu().numpy(), c.cpu().numpy())
     finally:
         eng.set_option(mt4g.OPT_CONF_MIN_PPM, 900000)
+
+
+def test_host_input_rejects_bad_batches_before_any_work(eng):
+    """Arguments a chunk would reject are rejected up front: nothing is enqueued."""
+    b = synth.generate(2, 45, 6)
+    steps = b.steps.copy()
+    steps[5] = 7  # the last series' sample count is no multiple of 7
+    with pytest.raises(mt4g.Mt4gError) as e:
+        eng.ks_segment_host(b.samples, b.offsets, steps, 1e-6, 1, 16, chunk_samples=1)
+    assert e.value.code == mt4g.EINVAL and "series 5" in str(e.value)
+    with pytest.raises(mt4g.Mt4gError) as e:
+        eng.ks_segment_host(b.samples, b.offsets, b.steps, 1.5, 1, 16)
+    assert e.value.code == mt4g.EINVAL
