@@ -23,10 +23,14 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-// Ascending bitonic sort of 32 V values; lane l holds elements l V .. l V + V - 1.
+// Ascending bitonic sort of 32 V values; lane l holds elements l V .. l V + V - 1.  The
+// direction of a compare-exchange depends on the element's index only through bits >= log2 V
+// in the stages that cross lanes and in every stage with k > V, so it is computed once per
+// lane and stage there; each exchange is then one min or max (selected by a predicate).
 template <int V>
 __device__ __forceinline__ void bitonic_sort_warp(uint32_t (&x)[V]) {
     const int lane = threadIdx.x & 31;
+    const int base = lane * V;
     constexpr int N = 32 * V;
 #pragma unroll
     for (int k = 2; k <= N; k <<= 1) {
@@ -37,23 +41,19 @@ __device__ __forceinline__ void bitonic_sort_warp(uint32_t (&x)[V]) {
                 for (int r = 0; r < V; r++) {
                     const int p = r ^ j;
                     if (p > r) {
-                        const bool up = ((lane * V + r) & k) == 0;
-                        const uint32_t a = x[r], b = x[p];
-                        if ((a > b) == up) {
-                            x[r] = b;
-                            x[p] = a;
-                        }
+                        const bool up = k < V ? ((r & k) == 0) : ((base & k) == 0);
+                        const uint32_t lo = min(x[r], x[p]), hi = max(x[r], x[p]);
+                        x[r] = up ? lo : hi;
+                        x[p] = up ? hi : lo;
                     }
                 }
             } else {
                 const int lj = j / V;
+                const bool takemin = ((base & k) == 0) == ((base & j) == 0);
 #pragma unroll
                 for (int r = 0; r < V; r++) {
-                    const int e = lane * V + r;
                     const uint32_t o = __shfl_xor_sync(kFull, x[r], lj);
-                    const bool up = (e & k) == 0;
-                    const bool lower = (e & j) == 0;
-                    x[r] = (lower == up) ? min(x[r], o) : max(x[r], o);
+                    x[r] = takemin ? min(x[r], o) : max(x[r], o);
                 }
             }
         }
