@@ -126,6 +126,8 @@ __global__ void __launch_bounds__(kTcThreads) conv_tc_kernel(const __nv_bfloat16
         const int64_t r0 = row_base(d, s) + t0;  // padded row of the window start of position t0
         const int nrows = min(kTcRows, d.T + 4 - t0);
         // the five shifted copies A_d[r] = row r + d of the tile, 16-byte chunks of 8 channels
+        // (unrolled so that several loads are in flight before their stores)
+#pragma unroll 5
         for (int e = tid; e < 5 * kTcTile * 4; e += kTcThreads) {
             const int dd = e / (kTcTile * 4), r = (e >> 2) % kTcTile, kc = e & 3;
             const int row = r + dd;
