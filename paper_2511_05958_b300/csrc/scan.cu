@@ -798,6 +798,9 @@ __device__ void slice_best(const RunParams &P, const SeriesDesc &d, int lo, int 
 
 // Persistent kernel: every warp independently takes tickets from the queue and processes
 // one item per ticket.  No block-level synchronisation.
+// LEARNED = false compiles the plain-segmentation kernel without the probe, certification and
+// refinement paths (fewer registers: no spills); learned calls launch the full one.
+template <bool LEARNED>
 __global__ void __launch_bounds__(kScanThreads, 4) queue_kernel(RunParams P, uint32_t epoch) {
     __shared__ WarpStage s_stage[kScanThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -844,7 +847,7 @@ __global__ void __launch_bounds__(kScanThreads, 4) queue_kernel(RunParams P, uin
         const bool wide = (uint64_t)d.m * H * H >= (1ull << 33);
         int nonempty = 0, bk = kNoK;
         uint64_t bg = 0;
-        if (kind == kGrid) {
+        if (LEARNED && kind == kGrid) {
             const int ng = min(kMaxGrid, B - A + 1);
             const int gk = lane < ng ? (ng == 1 ? A : A + (int)((int64_t)lane * (B - A) / (ng - 1))) : -1;
             const int gn = __shfl_down_sync(kFull, gk, 1);
@@ -878,7 +881,7 @@ __global__ void __launch_bounds__(kScanThreads, 4) queue_kernel(RunParams P, uin
                 else slice_best<false, 1>(P, d, lo, hi, k0, k0, kmax, stage, bk, bg, nonempty);
             }
             my_evals += (unsigned long long)(kmax - k0 + 1) * (unsigned long long)nonempty;
-        } else {  // window or refine slice: 32 explicit splits
+        } else if (LEARNED) {  // window or refine slice: 32 explicit splits
             const int k0 = it.k0;
             const int kmin = max(k0, A), kmax = min(k0 + 31, min(it.klim, B));
             if (wide) slice_best<true, 1>(P, d, lo, hi, k0, kmin, kmax, stage, bk, bg, nonempty);
@@ -912,7 +915,7 @@ __global__ void __launch_bounds__(kScanThreads, 4) queue_kernel(RunParams P, uin
                     }
                 }
                 warp_best(ck, cg, lo, hi);
-                if (kind == kPlain) {
+                if (!LEARNED || kind == kPlain) {
                     finish_segment(P, d, it.series, lo, hi, ck, cg, epoch);
                 } else if (kind == kRefine) {
                     const CertRecord *rec = P.recs + it.rec;
@@ -1015,13 +1018,16 @@ __global__ void collect_kernel(const SeriesDesc *__restrict__ desc, int64_t S, c
 int queue_grid(int device) {
     int sms = 0, per_sm = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, queue_kernel, kScanThreads, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, queue_kernel<true>, kScanThreads, 0) != cudaSuccess)
         return 0;
     return sms * (per_sm > 0 ? per_sm : 1);
 }
 
 cudaError_t launch_queue_run(const RunParams &P, int grid, uint32_t epoch, cudaStream_t st) {
-    queue_kernel<<<grid, kScanThreads, 0, st>>>(P, epoch);
+    if (P.mode == kRunLearned)
+        queue_kernel<true><<<grid, kScanThreads, 0, st>>>(P, epoch);
+    else
+        queue_kernel<false><<<grid, kScanThreads, 0, st>>>(P, epoch);
     return cudaGetLastError();
 }
 
