@@ -54,8 +54,8 @@ RECIPES = {2: "synth recipe 2 (T=512, m=128, levels 35/300/800/1100, 0.5% outlie
 # sort_series_kernel_1024x512x128.md, queue_kernel_learned_2048x512x128.md); keyed by (workload,
 # stage) and scaled by the number of series (the learned capture has 2048 of the 65,536 series).
 # Only workloads whose kernels were captured as they are now appear here; the others report null.
-NCU_TRAFFIC_PER_SERIES = {("plain", "queue"): 551.701248e6 / 1024, ("plain", "sort"): 1359.825152e6 / 1024,
-                          ("learned", "queue"): 2123.688768e6 / 2048}
+NCU_TRAFFIC_PER_SERIES = {("plain", "queue"): 480.339456e6 / 1024, ("plain", "sort"): 1363.369472e6 / 1024,
+                          ("learned", "queue"): 2125.035424e6 / 2048}
 STAGES = ["upload", "sort", "proposals", "queue", "collect"]
 
 
