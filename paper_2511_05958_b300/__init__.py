@@ -348,7 +348,9 @@ def _mixin_learned(cls):
         return out
 
     def latency_stats(self, samples, offsets, steps, stream=None, sync=True):
-        """mt4g_latency_stats: per-series (mean, p50, p95, std) device tensors."""
+        """mt4g_latency_stats: per-series (mean, p50, p95, std) device tensors.  mean and std are
+        float64; p50 and p95 hold the uint32 sample values in int32 tensors (bit patterns: view
+        them as uint32 on the host, e.g. t.cpu().numpy().view(np.uint32))."""
         import torch
         offsets, steps = _host_tables(offsets, steps)
         S = steps.shape[0]
