@@ -1,6 +1,9 @@
 // C ABI of libmt4g: context, argument validation, workspace, and the call sequence
 //   (reduce+rank for Eq. 2 mode) -> per-series radix sort + run table ->
-//   persistent work-queue kernel (scan, p-value, segmentation) -> collect.
+//   (learned mode: features -> tensor-core network -> windows) ->
+//   persistent work-queue kernel (scan, p-value, segmentation) -> collect,
+// plus CUDA-graph replay, the scan-tile autotuner, the host-input pipeline that overlaps
+// chunk copies with segmentation, the proposal network's training calls and measurement helpers.
 #include <algorithm>
 #include <map>
 #include <cstdarg>
