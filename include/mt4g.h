@@ -54,6 +54,7 @@ extern "C" {
 #define MT4G_ENOMEM (-3)    /* device or pinned-host allocation failed */
 #define MT4G_ECUDA (-4)     /* a CUDA runtime call failed; message in mt4g_last_error */
 #define MT4G_ETIMEOUT (-5)  /* a bounded device-side wait expired; outputs are incomplete */
+#define MT4G_ECHECK (-6)    /* a device consistency check (MT4G_OPT_CHECKS) failed; outputs are void */
 
 #define MT4G_MODE_FULL 0    /* every split of every segment is evaluated */
 #define MT4G_MODE_LEARNED 1 /* proposal windows + exact certification; same answers as FULL */
@@ -75,6 +76,10 @@ extern "C" {
                                     The first call with given arguments (pointers, sizes, host
                                     table contents, options, weights) is captured; identical calls
                                     replay it.  Stage timing is not recorded for graph calls. */
+#define MT4G_OPT_CHECKS 8        /* 1: after the per-series sort, one extra kernel checks what the
+                                    scan relies on (run table from 0 to N, strictly increasing;
+                                    labels < T; labels non-decreasing inside a run); a violation
+                                    makes mt4g_wait return MT4G_ECHECK.  Off by default. */
 
 typedef struct mt4g_ctx mt4g_ctx;
 

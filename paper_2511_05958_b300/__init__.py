@@ -16,7 +16,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmt4g.so")
 
-OK, EINVAL, ECAPACITY, ENOMEM, ECUDA, ETIMEOUT = 0, -1, -2, -3, -4, -5
+OK, EINVAL, ECAPACITY, ENOMEM, ECUDA, ETIMEOUT, ECHECK = 0, -1, -2, -3, -4, -5, -6
 MODE_FULL, MODE_LEARNED, MODE_REDUCED = 0, 1, 2
 OPT_WAIT_LIMIT_NS = 1
 OPT_STAGE_TIMING = 2
@@ -25,6 +25,7 @@ OPT_WINDOWS = 4
 OPT_HALF_WIDTH = 5
 OPT_CONF_MIN_PPM = 6
 OPT_GRAPH = 7
+OPT_CHECKS = 8
 MAX_STEPS = 32768
 FEAT_CHANNELS = 18
 CNN_PARAMS = 13377

@@ -72,6 +72,8 @@ struct mt4g_ctx {
     int ring_pos = 0;
     int ring_count = 0;
 
+    bool checks = false;  // MT4G_OPT_CHECKS: consistency check of the sort's output
+
     // CUDA-graph replay of identical calls (MT4G_OPT_GRAPH)
     bool use_graph = false;
     bool capturing = false;       // inside a capture: no host syncs, staging from graph_pin
@@ -465,6 +467,7 @@ int enqueue_pipeline(mt4g_ctx *ctx, const uint32_t *samples, Plan &P, RunParams 
         sort_in = B.rank;
     }
     CUDA_TRY(ctx, launch_sort(sort_in, B.desc, B.order, P.S, B.keyA, B.keyB, B.labA, B.labB, B.runs, st));
+    if (ctx->checks) CUDA_TRY(ctx, launch_check_sort(B.desc, P.S, B.labA, B.runs, &B.q->status, st));
     mark(ctx, 2, st);
 
     R = RunParams{};
@@ -603,6 +606,10 @@ int mt4g_set_option(mt4g_ctx *c, int option, int64_t value) {
         c->use_graph = value != 0;
         return MT4G_OK;
     }
+    if (option == MT4G_OPT_CHECKS) {
+        c->checks = value != 0;
+        return MT4G_OK;
+    }
     if (option == MT4G_OPT_WINDOWS) {
         if (value < 1 || value > 8) return fail(c, MT4G_EINVAL, "windows must be 1..8");
         c->n_win = (int32_t)value;
@@ -646,6 +653,7 @@ int mt4g_wait(mt4g_ctx *c) {
         c->n_chunk_hdr = 0;
     }
     const int32_t st = c->h_hdr->status;
+    if (st & kStatusCheck) return fail(c, MT4G_ECHECK, "device consistency check of the sort output failed");
     if (st & kStatusTimeout) return fail(c, MT4G_ETIMEOUT, "a bounded device-side wait expired");
     if (st & kStatusQueueFull) return fail(c, MT4G_ECAPACITY, "work queue capacity exceeded");
     if (st & kStatusCapacity) return fail(c, MT4G_ECAPACITY, "a series has more than max_cp change points");
@@ -821,6 +829,7 @@ uint64_t call_key(const mt4g_ctx *ctx, int entry, const void *samples, const int
     h = fnv_val(h, ctx->half);
     h = fnv_val(h, ctx->conf_min);
     h = fnv_val(h, ctx->forced_kpt);
+    h = fnv_val(h, ctx->checks);
     h = fnv_val(h, ctx->cnn_version);
     for (int i = 0; i < n_outs; i++) h = fnv_val(h, outs[i]);
     if (S > 0 && offsets && steps) {

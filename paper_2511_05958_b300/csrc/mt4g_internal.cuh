@@ -83,7 +83,7 @@ struct ChunkResult {
     uint64_t g;  // max_x |H c_L - (k - lo) C|; the exact numerator is m * g
 };
 
-enum : int32_t { kStatusTimeout = 1, kStatusQueueFull = 2, kStatusCapacity = 4 };
+enum : int32_t { kStatusTimeout = 1, kStatusQueueFull = 2, kStatusCapacity = 4, kStatusCheck = 8 };
 
 struct QueueHeader {
     unsigned long long head;     // next ticket to hand out
@@ -151,6 +151,10 @@ cudaError_t launch_init_learned(const RunParams &P, const float *conf, float con
                                 int64_t S, uint32_t epoch, cudaStream_t st);
 int queue_grid(int device);
 
+// Consistency check of the sort's output (MT4G_OPT_CHECKS): run table, labels.  Sets
+// kStatusCheck in *status on any violation; reads only within each series' own ranges.
+cudaError_t launch_check_sort(const SeriesDesc *desc, int64_t S, const uint16_t *lab, const int32_t *runs,
+                              int32_t *status, cudaStream_t st);
 cudaError_t launch_collect(const SeriesDesc *desc, int64_t S, const uint8_t *cp_flag, const int64_t *cp_num,
                            const int64_t *cp_den, const double *cp_p, int32_t max_cp, int32_t *cp_count,
                            int32_t *cp_idx, int64_t *dnum, int64_t *dden, double *p, QueueHeader *q,

@@ -399,7 +399,52 @@ reduce_rank_kernel(const uint32_t *__restrict__ samples, const SeriesDesc *__res
     }
 }
 
+// Invariants the scan relies on, checked per series (one CTA): the run table starts at 0,
+// increases strictly and ends at N with nruns entries; every label is a step index (< T);
+// labels are non-decreasing within each run (sample i and i - 1 in the same run, found by
+// binary search in the validated table).  Reads stay inside the series' label range
+// [off, off + N) and run-table range [run_base, run_base + nruns].
+__global__ void __launch_bounds__(256) check_sort_kernel(const SeriesDesc *__restrict__ desc,
+                                                         const uint16_t *__restrict__ lab,
+                                                         const int32_t *__restrict__ runs, int32_t *status) {
+    const SeriesDesc d = desc[blockIdx.x];
+    const int64_t N = (int64_t)d.T * d.m;
+    const int32_t U = d.nruns;
+    const int32_t *rt = runs + d.run_base;
+    const uint16_t *l = lab + d.off;
+    bool bad = U < 1 || U > N;
+    if (!bad) {
+        if (threadIdx.x == 0) bad = rt[0] != 0 || rt[U] != N;
+        for (int32_t j = threadIdx.x; j < U && !bad; j += blockDim.x) bad = rt[j] >= rt[j + 1];
+        for (int64_t i = threadIdx.x; i < N && !bad; i += blockDim.x) bad = l[i] >= d.T;
+    }
+    if (!__syncthreads_or(bad)) {
+        for (int64_t i = 1 + threadIdx.x; i < N && !bad; i += blockDim.x) {
+            int32_t lo = 0, hi = U;  // rt[lo] <= i < rt[hi]
+            while (hi - lo > 1) {
+                const int32_t mid = (lo + hi) >> 1;
+                if (rt[mid] <= i)
+                    lo = mid;
+                else
+                    hi = mid;
+            }
+            bad = rt[lo] != i && l[i - 1] > l[i];
+        }
+        bad = __syncthreads_or(bad);
+    } else {
+        bad = true;
+    }
+    if (bad && threadIdx.x == 0) atomicOr(status, (int32_t)kStatusCheck);
+}
+
 }  // namespace
+
+cudaError_t launch_check_sort(const SeriesDesc *desc, int64_t S, const uint16_t *lab, const int32_t *runs,
+                              int32_t *status, cudaStream_t st) {
+    if (S <= 0) return cudaSuccess;
+    check_sort_kernel<<<(unsigned)S, 256, 0, st>>>(desc, lab, runs, status);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_sort(const uint32_t *samples, SeriesDesc *desc, const int32_t *order, int64_t S,
                         uint32_t *keyA, uint32_t *keyB, uint16_t *labA, uint16_t *labB, int32_t *runs,

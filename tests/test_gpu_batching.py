@@ -141,3 +141,29 @@ def test_host_input_rejects_bad_batches_before_any_work(eng):
     with pytest.raises(mt4g.Mt4gError) as e:
         eng.ks_segment_host(b.samples, b.offsets, b.steps, 1.5, 1, 16)
     assert e.value.code == mt4g.EINVAL
+
+
+def test_consistency_checks_pass_and_change_nothing(eng):
+    """MT4G_OPT_CHECKS: the sort-output check passes on every workload shape (equal-value runs,
+    uneven series, the reduced path, host input) and leaves every answer unchanged."""
+    import torch
+    eng.cnn_init(8)
+    for cfg, seed, S in ((1, 51, 40), (2, 52, 40), (3, 53, 24)):
+        b = synth.generate(cfg, seed, S)
+        d = mt4g.to_device_samples(b.samples)
+        for mode in (mt4g.MODE_FULL, mt4g.MODE_REDUCED, mt4g.MODE_LEARNED):
+            eng.set_option(mt4g.OPT_CHECKS, 0)
+            r0, ref = _seg(eng, d, b, mode=mode)
+            sc0 = eng.ks_scan(d, b.offsets, b.steps) if mode == mt4g.MODE_FULL else None
+            eng.set_option(mt4g.OPT_CHECKS, 1)
+            r1, got = _seg(eng, d, b, mode=mode)
+            assert r1.rc == r0.rc and eng.wait() == r0.rc
+            _same(ref, got)
+            if sc0 is not None:
+                sc1 = eng.ks_scan(d, b.offsets, b.steps)
+                _same([t.cpu().numpy() for t in sc0], [t.cpu().numpy() for t in sc1])
+        host = torch.from_numpy(b.samples.view(np.int32)).pin_memory()
+        r2 = eng.ks_segment_host(host, b.offsets, b.steps, 1e-6, 1, 16, chunk_samples=3 * 65536 + 1)
+        eng.set_option(mt4g.OPT_CHECKS, 0)
+        _, ref2 = _seg(eng, d, b)
+        _same(ref2, [t.cpu().numpy() for t in r2[1:6]])
