@@ -61,13 +61,22 @@ extern "C" {
 #define MT4G_MODE_REDUCED 2 /* Eq. 2 reduction first: one FP64 value per step, then the same test */
 
 #define MT4G_MAX_STEPS 32768
+
+/* Scan tile value of the run sweep: one warp walks all splits of a segment in order, moving
+   one step's samples to the left part at a time.  It applies to series with at most 1536
+   distinct values and to segments with m H^2 < 2^31; other segments of such series are
+   scanned in 32-split slices.  Where the autotuner has no entry, full and reduced calls plan
+   it for series of at most 2^17 samples and use it when those carry at least half of the
+   call's T^2 m; learned calls scan in slices. */
+#define MT4G_SCAN_SWEEP 8
 #define MT4G_MAX_SERIES_SAMPLES (1LL << 30)
 
 /* Options for mt4g_set_option. */
 #define MT4G_OPT_WAIT_LIMIT_NS 1 /* bound on any device-side wait in the work queue (default 5e9 ns) */
 #define MT4G_OPT_STAGE_TIMING 2  /* 1: record CUDA events between the stages of every call */
 #define MT4G_OPT_SCAN_KPT 3      /* scan tile: 0 = per-series choice (default), else 1, 2 or 4
-                                    groups of 32 splits per warp work item for every series */
+                                    groups of 32 splits per warp work item, or MT4G_SCAN_SWEEP,
+                                    for every series */
 #define MT4G_OPT_WINDOWS 4       /* learned mode: proposal windows per series (default 3) */
 #define MT4G_OPT_HALF_WIDTH 5    /* learned mode: window half width in steps (default 16) */
 #define MT4G_OPT_CONF_MIN_PPM 6  /* learned mode: series whose window mass is below this (in
@@ -227,13 +236,14 @@ int mt4g_propose(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets,
                  int32_t n_win, int32_t half_width, int32_t *win_center, float *conf, void *cuda_stream);
 
 /*
- * Scan-tile autotuner (no counterpart in the paper).  The work queue scans each segment in
- * warp items of 32, 64 or 128 splits (the tile).  mt4g_autotune times mt4g_ks_scan with each
- * tile on up to 256 series of every (floor log2 T, floor log2 m) bucket present in the batch
- * (copied into a temporary buffer) and keeps the fastest tile per bucket in the context;
- * later calls use it for series of that bucket (default 32 splits).  Synchronises the
- * stream.  The table can be written to and read from a text file; mt4g_autotune_get returns
- * the tile (1, 2 or 4 groups of 32) used for a shape.
+ * Scan-tile autotuner (no counterpart in the paper).  The work queue scans each segment
+ * either by the run sweep (MT4G_SCAN_SWEEP, one item per segment) or in warp items of 32, 64
+ * or 128 splits (the tile).  mt4g_autotune times mt4g_ks_scan with each choice on up to 256
+ * series of every (floor log2 T, floor log2 m) bucket present in the batch (copied into a
+ * temporary buffer) and keeps the fastest per bucket in the context; later calls use it for
+ * series of that bucket (default: the run sweep).  Synchronises the stream.  The table can be
+ * written to and read from a text file; mt4g_autotune_get returns the choice (1, 2 or 4
+ * groups of 32, or MT4G_SCAN_SWEEP) used for a shape.
  */
 int mt4g_autotune(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets, const int32_t *steps, int64_t S,
                   void *cuda_stream);

@@ -23,7 +23,8 @@ using namespace mt4g;
 
 struct mt4g_ctx {
     int device = 0;
-    int grid = 0;
+    int grid = 0;        // CTAs of the slice-only queue kernel
+    int grid_sweep = 0;  // CTAs of the queue kernel with the run sweep
     std::string err;
     long long wait_limit_ns = 5000000000LL;
 
@@ -149,6 +150,7 @@ struct Plan {
     int64_t n_init = 0;                // top-level slices
     unsigned long long cap = 0;
     bool learned = false;              // items are pushed by the learned init kernel
+    bool use_sweep = false;            // run-sweep series present: ranks from the sort, sweep kernel
     unsigned long long rec_cap = 0;    // certification records (learned mode)
 };
 
@@ -218,10 +220,12 @@ int ilog2(int64_t v) {
     return b;
 }
 
+constexpr int64_t kSweepLikelySamples = 1 << 17;
+
 int32_t pick_kpt(const mt4g_ctx *ctx, int32_t T, int32_t m) {
     if (ctx->forced_kpt) return ctx->forced_kpt;
     const auto it = ctx->tune.find({ilog2(T), ilog2(m)});
-    return it == ctx->tune.end() ? 1 : it->second;
+    return it == ctx->tune.end() ? MT4G_SCAN_SWEEP : it->second;
 }
 
 // Validate the host tables and build the per-call plan.
@@ -269,13 +273,41 @@ int make_plan(mt4g_ctx *ctx, const int64_t *offsets, const int32_t *steps, int64
             d.m = m;
         }
         d.run_base = d.off + s;
-        d.kpt = pick_kpt(ctx, d.T, d.m);
+        const int32_t tile = pick_kpt(ctx, d.T, d.m);
+        d.kpt = tile == MT4G_SCAN_SWEEP ? 0 : tile;
         P.desc[s] = d;
         sumT += T;
         ntot += (int64_t)d.T * d.m;
     }
     P.sumT = sumT;
     P.Ntot = ntot;
+    // Run sweep or slices.  The sweep needs at most kSweepMaxRuns distinct values, which the
+    // host cannot see before the sort; by default it is planned for series of at most
+    // kSweepLikelySamples samples (a forced or tuned sweep is planned as asked), and taken
+    // for the call when those series carry at least half of the estimated scan cost (T^2 m):
+    // the sweep kernel holds fewer warps per SM, which would slow the slices of the others.
+    // Series planned for the sweep that turn out to have more distinct values are scanned in
+    // slices by that kernel.  Learned calls keep the slice kernel (their probes are slices).
+    {
+        const bool forced = ctx->forced_kpt != 0;
+        double sw = 0.0, tot = 0.0;
+        for (int64_t s = 0; s < S; s++) {
+            SeriesDesc &d = P.desc[s];
+            const double cost = (double)d.T * d.T * d.m;
+            tot += cost;
+            if (d.kpt != 0) continue;
+            const bool tuned = ctx->tune.count({ilog2(d.T), ilog2(d.m)}) != 0;
+            if (!forced && !tuned && (int64_t)d.T * d.m > kSweepLikelySamples)
+                d.kpt = 1;
+            else
+                sw += cost;
+        }
+        P.use_sweep = mode != MT4G_MODE_LEARNED && sw > 0.0 &&
+                      (ctx->forced_kpt == MT4G_SCAN_SWEEP || sw >= 0.5 * tot);
+        if (!P.use_sweep)
+            for (auto &d : P.desc)
+                if (d.kpt == 0) d.kpt = 1;
+    }
     // sort launch order: largest series first
     P.sort_order.resize(S);
     std::iota(P.sort_order.begin(), P.sort_order.end(), 0);
@@ -466,13 +498,15 @@ int enqueue_pipeline(mt4g_ctx *ctx, const uint32_t *samples, Plan &P, RunParams 
         CUDA_TRY(ctx, launch_reduce_rank(samples, B.raw_desc, P.S, B.red, B.rank, st));
         sort_in = B.rank;
     }
-    CUDA_TRY(ctx, launch_sort(sort_in, B.desc, B.order, P.S, B.keyA, B.keyB, B.labA, B.labB, B.runs, st));
+    CUDA_TRY(ctx, launch_sort(sort_in, B.desc, B.order, P.S, B.keyA, B.keyB, B.labA, B.labB, B.runs, P.use_sweep,
+                              st));
     if (ctx->checks) CUDA_TRY(ctx, launch_check_sort(B.desc, P.S, B.labA, B.runs, &B.q->status, st));
     mark(ctx, 2, st);
 
     R = RunParams{};
     R.desc = B.desc;
     R.lab = B.labA;
+    R.rk = P.use_sweep ? B.labB : nullptr;
     R.runs = B.runs;
     R.q = B.q;
     R.items = B.items;
@@ -533,7 +567,8 @@ int mt4g_create(mt4g_ctx **out, int device) {
     }
     memset(c->h_hdr, 0, sizeof(QueueHeader));
     c->grid = queue_grid(device);
-    if (c->grid <= 0) {
+    c->grid_sweep = queue_grid_sweep(device);
+    if (c->grid <= 0 || c->grid_sweep <= 0) {
         delete c;
         return MT4G_ECUDA;
     }
@@ -597,8 +632,9 @@ int mt4g_set_option(mt4g_ctx *c, int option, int64_t value) {
         return MT4G_OK;
     }
     if (option == MT4G_OPT_SCAN_KPT) {
-        if (value != 0 && value != 1 && value != 2 && value != 4)
-            return fail(c, MT4G_EINVAL, "scan tile must be 0 (automatic), 1, 2 or 4");
+        if (value != 0 && value != 1 && value != 2 && value != 4 && value != MT4G_SCAN_SWEEP)
+            return fail(c, MT4G_EINVAL, "scan tile must be 0 (automatic), 1, 2, 4 or %d (run sweep)",
+                        MT4G_SCAN_SWEEP);
         c->forced_kpt = (int32_t)value;
         return MT4G_OK;
     }
@@ -682,7 +718,7 @@ static int scan_body(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offs
     R.dden_out = dden_out;
     R.p_out = p_out;
     mark(ctx, 3, st);
-    CUDA_TRY(ctx, launch_queue_run(R, ctx->grid, (uint32_t)epoch, st));
+    CUDA_TRY(ctx, launch_queue_run(R, R.rk ? ctx->grid_sweep : ctx->grid, (uint32_t)epoch, st));
     mark(ctx, 4, st);
     return finish_call(ctx, B, st);
 }
@@ -724,7 +760,7 @@ static int segment_body(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *o
         CUDA_TRY(ctx, cudaMemsetAsync(B.fallback, 0, P.S * sizeof(int32_t), st));
     }
     if (!P.learned) mark(ctx, 3, st);
-    CUDA_TRY(ctx, launch_queue_run(R, ctx->grid, (uint32_t)epoch, st));
+    CUDA_TRY(ctx, launch_queue_run(R, R.rk ? ctx->grid_sweep : ctx->grid, (uint32_t)epoch, st));
     mark(ctx, 4, st);
     CUDA_TRY(ctx, launch_collect(B.desc, P.S, B.cp_flag, B.cp_num, B.cp_den, B.cp_p, max_cp, cp_count, cp_idx, dnum,
                                  dden, p, B.q, st));
@@ -1630,8 +1666,8 @@ extern "C" int mt4g_autotune(mt4g_ctx *ctx, const uint32_t *samples, const int64
             }
         if (rc) break;
         float best_ms = 1e30f;
-        int32_t best = 1;
-        for (int32_t kpt : {1, 2, 4}) {
+        int32_t best = MT4G_SCAN_SWEEP;
+        for (int32_t kpt : {MT4G_SCAN_SWEEP, 1, 2, 4}) {
             ctx->forced_kpt = kpt;
             float ms = 0.f;
             for (int rep = 0; rep < 3 && !rc; rep++) {  // first call warms up, the minimum of the rest counts
@@ -1684,7 +1720,7 @@ extern "C" int mt4g_autotune_load(mt4g_ctx *ctx, const char *path) {
     while (fgets(line, sizeof(line), f)) {
         if (line[0] == '#') continue;
         int a = 0, b = 0, k = 0;
-        if (sscanf(line, "%d %d %d", &a, &b, &k) != 3 || (k != 1 && k != 2 && k != 4)) {
+        if (sscanf(line, "%d %d %d", &a, &b, &k) != 3 || (k != 1 && k != 2 && k != 4 && k != MT4G_SCAN_SWEEP)) {
             fclose(f);
             return fail(ctx, MT4G_EINVAL, "%s: bad line", path);
         }

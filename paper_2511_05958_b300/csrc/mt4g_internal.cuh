@@ -24,6 +24,13 @@ constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 samples per tile
 
 constexpr int kScanThreads = 256;  // CTA of the persistent kernel: 8 independent warps
 
+// Run sweep of the scan: a series with at most kSweepMaxRuns distinct values gets, from the
+// sort, the run index of every sample in input order (labB), and its segments are scanned
+// by one warp that keeps the segment's runs in shared memory.  The kernel with the sweep
+// runs CTAs of kSweepThreads (its per-warp shared memory is larger).
+constexpr int kSweepMaxRuns = 1536;
+constexpr int kSweepThreads = 64;
+
 struct SeriesDesc {
     int64_t off;        // first sample of the series
     int64_t step_base;  // first per-step slot of the series (prefix sum of T)
@@ -31,7 +38,9 @@ struct SeriesDesc {
     int32_t T;          // steps
     int32_t m;          // samples per step
     int32_t nruns;      // U_s, number of distinct values (written by the sort)
-    int32_t kpt;        // split groups of 32 per warp work item (1, 2 or 4): the scan tile
+    int32_t kpt;        // scan tile: split groups of 32 per warp work item (1, 2 or 4), or 0 for
+                        // the run sweep (one item per segment; slices of 32 splits when the
+                        // series or segment does not qualify)
     uint32_t median;    // sorted value at index N / 2 (written by the sort)
     uint32_t p50;       // nearest-rank order statistics sorted[ceil(q N) - 1], q = 1/2 and
     uint32_t p95;       // 95/100 (written by the sort)
@@ -104,6 +113,7 @@ enum RunMode : int32_t { kRunScan = 0, kRunSegment = 1, kRunLearned = 2 };
 struct RunParams {
     const SeriesDesc *desc;
     const uint16_t *lab;   // sorted labels (labA)
+    const uint16_t *rk;    // run index of every sample in input order (labB), or null: no sweep
     const int32_t *runs;   // run table
     QueueHeader *q;
     WorkItem *items;
@@ -134,13 +144,16 @@ struct RunParams {
 // Number of slices of a segment of H steps (0 if it cannot be split).
 __host__ __device__ inline int32_t seg_chunks(int32_t H, int32_t min_seg, int32_t kpt) {
     const int32_t nk = H - 2 * min_seg + 1;
+    if (kpt == 0) return nk <= 0 ? 0 : 1;  // run sweep: the whole segment
     const int32_t w = 32 * kpt;
     return nk <= 0 ? 0 : (nk + w - 1) / w;
 }
 
 // ---- kernels (launch wrappers live in the .cu files) ----
+// ranks: also write every sample's run index to labB for series with at most
+// kSweepMaxRuns distinct values (the run sweep's input).
 cudaError_t launch_sort(const uint32_t *samples, SeriesDesc *desc, const int32_t *order, int64_t S,
-                        uint32_t *keyA, uint32_t *keyB, uint16_t *labA, uint16_t *labB, int32_t *runs,
+                        uint32_t *keyA, uint32_t *keyB, uint16_t *labA, uint16_t *labB, int32_t *runs, bool ranks,
                         cudaStream_t st);
 
 cudaError_t launch_queue_run(const RunParams &P, int grid, uint32_t epoch, cudaStream_t st);
@@ -149,7 +162,8 @@ cudaError_t launch_init_items(const SeriesDesc *desc, const int32_t *qorder, con
                               cudaStream_t st);
 cudaError_t launch_init_learned(const RunParams &P, const float *conf, float conf_min, int32_t *fallback_out,
                                 int64_t S, uint32_t epoch, cudaStream_t st);
-int queue_grid(int device);
+int queue_grid(int device);        // CTAs of the slice-only kernel
+int queue_grid_sweep(int device);  // CTAs of the kernel with the run sweep
 
 // Consistency check of the sort's output (MT4G_OPT_CHECKS): run table, labels.  Sets
 // kStatusCheck in *status on any violation; reads only within each series' own ranges.

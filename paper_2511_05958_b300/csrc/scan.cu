@@ -10,7 +10,10 @@
 // when m H^2 < 2^33 the difference is exact in wrapping 32-bit arithmetic; larger
 // shapes take the 64-bit path.
 //
-// Each lane of a warp owns one split k.  The warp walks the series' runs of equal
+// Two ways to get g_k for every split.  Run sweep (series with at most kSweepMaxRuns
+// distinct values, narrow shapes): one warp per segment walks the splits in order and moves
+// one step's samples into the left part at a time (see sweep_best).  Slices (the rest): each
+// lane of a warp owns one split k.  The warp walks the series' runs of equal
 // values (the run table built by the sort) in value order, so x takes every distinct
 // value of the series; values absent from the segment leave the counts unchanged and
 // cannot raise the maximum.  Within a run the labels are sorted, so the in-segment
@@ -556,6 +559,215 @@ __device__ __forceinline__ void warp_best(int &bk, uint64_t &bg, int lo, int hi)
     }
 }
 
+// ---------------------------------------------------------------- run sweep
+//
+// The same g_k for every split of a segment, by one warp walking the splits in order.  The
+// segment's runs with in-segment samples are numbered c = 0 .. U'-1 in value order, and for
+// split k (a = k - lo)
+//     v_k(c) = H c_L(x_c) - a C(x_c) = sum_{c' <= c} l_k(c') - a C_c,
+// with l_k(c') = H times the left samples of run c' and C_c the in-segment samples of runs
+// up to c.  Going from split k to k + 1 moves the m samples of step k to the left part: each
+// adds H to l at its own run (the run index of every sample comes from the sort), so an
+// update costs O(m), and the values at all runs follow from one pass over l.
+//
+// Lane L owns a contiguous block of runs [b0, b1).  Within the block it accumulates the
+// values relative to the run before the block,
+//     v_k(c) - v_k(b0 - 1) = sum_{b0 <= c' <= c} l_k(c') - a (C_c - C_{b0-1}),
+// a sum over the block's samples of H (left) or 0, minus a each, so below m H^2 in magnitude,
+// and keeps their max and min.  The block's own sum of l, scanned across the warp, then
+// gives v_k(b0 - 1) and so the block's true max and min; the warp maximum of the moduli is
+// g_k.  The sweep takes segments with m H^2 < 2^31, where every quantity above is an exact
+// 32-bit integer.
+struct __align__(16) SweepStage {
+    uint2 lc[kSweepMaxRuns];      // (l, C) of compact run c; during setup .x counts run r
+    uint16_t map[kSweepMaxRuns];  // run -> compact run
+};
+
+union __align__(16) WarpSmem {
+    WarpStage ws;
+    SweepStage ss;
+};
+
+__device__ __forceinline__ bool sweepable(const RunParams &P, const SeriesDesc &d, int H) {
+    return P.rk != nullptr && d.nruns <= kSweepMaxRuns && (uint64_t)d.m * (uint64_t)H * (uint64_t)H < (1ull << 31);
+}
+
+// Scan tile in effect for a segment of H steps: the series' tile, or for run-sweep series
+// the sweep where the segment qualifies and single 32-split slices where it does not.
+__device__ __forceinline__ int eff_kpt(const RunParams &P, const SeriesDesc &d, int H) {
+    return d.kpt ? d.kpt : (sweepable(P, d, H) ? 0 : 1);
+}
+
+// lc[idx].x += w for every active lane.  A shared-memory reduction without return: the warp
+// does not wait for it, and lanes that hit the same run are serialised by the hardware.
+__device__ __forceinline__ void lc_add(SweepStage &ss, uint32_t idx, uint32_t w, bool act) {
+    if (act) atomicAdd(&ss.lc[idx].x, w);
+}
+
+constexpr int kSweepPre = 8;  // run indices of one step held per lane (steps of up to 256 samples)
+
+// Run indices of step t into registers: slot q holds sample lane + 32 q.
+__device__ __forceinline__ void sweep_load_step(const uint16_t *__restrict__ rk, int64_t t, int m, int lane,
+                                                uint32_t (&buf)[kSweepPre]) {
+    const uint16_t *src = rk + t * (int64_t)m;
+#pragma unroll
+    for (int q = 0; q < kSweepPre; q++) {
+        const int j = lane + 32 * q;
+        buf[q] = j < m ? (uint32_t)__ldg(src + j) : 0u;
+    }
+}
+
+// Move the samples of step t to the left part: l grows by H at each sample's run.  `buf`
+// holds the step's first 256 run indices (sweep_load_step); the rest are read here.
+__device__ __forceinline__ void sweep_apply_step(SweepStage &ss, const uint16_t *__restrict__ rk, int64_t t, int m,
+                                                 uint32_t H, int lane, const uint32_t (&buf)[kSweepPre]) {
+#pragma unroll
+    for (int q = 0; q < kSweepPre; q++) {
+        if (32 * q < m) {
+            const bool act = lane + 32 * q < m;
+            lc_add(ss, act ? (uint32_t)ss.map[buf[q]] : 0u, H, act);
+        }
+    }
+    const uint16_t *src = rk + t * (int64_t)m;
+    for (int j0 = 32 * kSweepPre; j0 < m; j0 += 32) {
+        const bool act = j0 + lane < m;
+        lc_add(ss, act ? (uint32_t)ss.map[__ldg(src + j0 + lane)] : 0u, H, act);
+    }
+}
+
+// Best split (k, g) over A <= k <= B of segment [lo, hi) of a run-sweep series; every lane
+// gets it.  `nonempty` = U', the runs with in-segment samples.
+__device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int hi, int A, int B, SweepStage &ss,
+                           int &bk, uint64_t &bg, int &nonempty) {
+    const int lane = threadIdx.x & 31;
+    const int U = d.nruns, m = d.m;
+    const uint16_t *__restrict__ rk = P.rk + d.off;
+    const uint32_t H = (uint32_t)(hi - lo);
+    const unsigned lt = lanemask_lt();
+
+    // in-segment samples per run, into lc[r].x
+    if (lo == 0 && hi == d.T) {
+        const int32_t *rt = P.runs + d.run_base;
+        for (int r = lane; r < U; r += 32) ss.lc[r].x = (uint32_t)(__ldg(rt + r + 1) - __ldg(rt + r));
+    } else {
+        for (int r = lane; r < U; r += 32) ss.lc[r].x = 0;
+        __syncwarp();
+        const int64_t e1 = (int64_t)hi * m;
+        for (int64_t e0 = (int64_t)lo * m; e0 < e1; e0 += 512) {  // 16 loads in flight per lane
+            uint32_t r16[16];
+#pragma unroll
+            for (int q = 0; q < 16; q++) {
+                const int64_t e = e0 + 32 * q + lane;
+                r16[q] = e < e1 ? (uint32_t)__ldg(rk + e) : 0u;
+            }
+#pragma unroll
+            for (int q = 0; q < 16; q++) lc_add(ss, r16[q], 1u, e0 + 32 * q + lane < e1);
+        }
+    }
+    __syncwarp();
+    // compaction, 32 runs per round: a run's compact slot is never above its own index, and
+    // every round reads its counts before it writes, so the later rounds' counts survive
+    uint32_t nc = 0, cs = 0;  // runs kept so far, in-segment samples so far
+    for (int r0 = 0; r0 < U; r0 += 32) {
+        const int r = r0 + lane;
+        const uint32_t n = r < U ? ss.lc[r].x : 0u;
+        const unsigned keep = __ballot_sync(kFull, n != 0);
+        uint32_t incl = n;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        __syncwarp();
+        if (n != 0) {
+            const uint32_t ci = nc + (uint32_t)__popc(keep & lt);
+            ss.map[r] = (uint16_t)ci;
+            ss.lc[ci] = make_uint2(0u, cs + incl);
+        }
+        nc += (uint32_t)__popc(keep);
+        cs += __shfl_sync(kFull, incl, 31);
+        __syncwarp();
+    }
+    const int Uc = (int)nc;
+    nonempty = Uc;
+    // an odd count is padded with a copy of the last run (l = 0, same C): it repeats the
+    // last value and changes no maximum, and lets every block read whole pairs
+    const int Ue = Uc + (Uc & 1);
+    if ((Uc & 1) && lane == 0) ss.lc[Uc] = make_uint2(0u, cs);
+    // blocks: R runs per lane, R even; R = 2 mod 4 for larger R keeps the 16-byte pair loads of
+    // a quarter warp on distinct banks
+    int R = (Ue + 31) / 32;
+    R += R & 1;
+    if (R >= 8 && (R & 3) == 0) R += 2;
+    const int b0 = min(lane * R, Ue), b1 = min(b0 + R, Ue);
+    const int npair = (b1 - b0) >> 1;
+    const uint4 *pairs = reinterpret_cast<const uint4 *>(&ss.lc[b0]);
+    __syncwarp();
+    const uint32_t Cb = b0 > 0 ? ss.lc[b0 - 1].y : 0u;  // in-segment samples below the block
+
+    for (int t = lo; t < A; t++) {
+        uint32_t buf[kSweepPre];
+        sweep_load_step(rk, t, m, lane, buf);
+        sweep_apply_step(ss, rk, t, m, H, lane, buf);
+    }
+    uint32_t nxt[kSweepPre];
+    sweep_load_step(rk, A, m, lane, nxt);
+    bk = kNoK;
+    bg = 0;
+    uint32_t gk = 0;  // g of split kb + lane
+    int kb = A;
+    for (int k = A; k <= B; k++) {
+        uint32_t cur[kSweepPre];
+#pragma unroll
+        for (int q = 0; q < kSweepPre; q++) cur[q] = nxt[q];
+        if (k + 1 <= B) sweep_load_step(rk, k + 1, m, lane, nxt);  // in flight during this split
+        __syncwarp();
+        const uint32_t a = (uint32_t)(k - lo), na = 0u - a;
+        const uint32_t h0 = a * Cb;
+        uint32_t hc = h0;
+        int32_t mx = INT_MIN, mn = INT_MAX;
+#pragma unroll 4
+        for (int j = 0; j < npair; j++) {
+            const uint4 q = pairs[j];
+            hc += q.x;
+            const int32_t v0 = (int32_t)(hc + na * q.y);
+            hc += q.z;
+            const int32_t v1 = (int32_t)(hc + na * q.w);
+            mx = max(mx, max(v0, v1));
+            mn = min(mn, min(v0, v1));
+        }
+        const uint32_t blk = hc - h0;  // sum of l over the block
+        // every lane has read l for split k: step k's samples move left now (reductions the warp
+        // does not wait for), and the warp's results for split k follow in registers
+        __syncwarp();
+        if (k < B) sweep_apply_step(ss, rk, k, m, H, lane, cur);
+        uint32_t incl = blk;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const uint32_t vs = (incl - blk) - a * Cb;  // v_k at the run before the block
+        uint32_t gl = 0;
+        if (npair > 0) {
+            const int32_t bmax = (int32_t)(vs + (uint32_t)mx), bmin = (int32_t)(vs + (uint32_t)mn);
+            gl = max((uint32_t)max(bmax, 0), (uint32_t)max(-bmin, 0));
+        }
+        const uint32_t g = __reduce_max_sync(kFull, gl);
+        if (lane == k - kb) gk = g;
+        if (k - kb == 31 || k == B) {
+            const int kk = kb + lane;
+            if (kk <= k && better(kk, (uint64_t)gk, bk, bg, lo, hi)) {
+                bk = kk;
+                bg = gk;
+            }
+            kb = k + 1;
+        }
+    }
+    warp_best(bk, bg, lo, hi);
+    __syncwarp();
+}
+
 // Reserve `tot` queue slots and count them as pending (one lane).  Returns the first slot,
 // or ~0 when the queue is full (then nothing is pending and the status says so).
 __device__ unsigned long long reserve_slots(const RunParams &P, int tot) {
@@ -585,7 +797,7 @@ __device__ __noinline__ void push_segment(const RunParams &P, const SeriesDesc &
     if (B < A) return;
     const bool learned = P.mode == kRunLearned && !P.fallback[series];
     if (!learned) {
-        const int nch = seg_chunks(hi - lo, P.min_seg, d.kpt);
+        const int nch = seg_chunks(hi - lo, P.min_seg, eff_kpt(P, d, hi - lo));
         unsigned long long base = 0;
         if (lane == 0) base = reserve_slots(P, nch);
         base = __shfl_sync(kFull, base, 0);
@@ -605,7 +817,7 @@ __device__ __noinline__ void push_segment(const RunParams &P, const SeriesDesc &
         inner = c >= A + P.half / 2 && c <= B - P.half / 2;
     }
     if (__ballot_sync(kFull, inner) == 0) {
-        const int nch = seg_chunks(hi - lo, P.min_seg, d.kpt);
+        const int nch = seg_chunks(hi - lo, P.min_seg, eff_kpt(P, d, hi - lo));
         unsigned long long base = 0;
         if (lane == 0) base = reserve_slots(P, nch);
         base = __shfl_sync(kFull, base, 0);
@@ -800,11 +1012,16 @@ __device__ void slice_best(const RunParams &P, const SeriesDesc &d, int lo, int 
 // one item per ticket.  No block-level synchronisation.
 // LEARNED = false compiles the plain-segmentation kernel without the probe, certification and
 // refinement paths (fewer registers: no spills); learned calls launch the full one.
-template <bool LEARNED>
-__global__ void __launch_bounds__(kScanThreads, 4) queue_kernel(RunParams P, uint32_t epoch) {
-    __shared__ WarpStage s_stage[kScanThreads / 32];
+// SWEEP = true adds the run sweep: each warp's shared memory then holds a SweepStage (for
+// up to kSweepMaxRuns runs), launched as CTAs of kSweepThreads; without it, the smaller
+// slice staging allows more resident warps.
+template <bool LEARNED, bool SWEEP>
+__global__ void __launch_bounds__(SWEEP ? kSweepThreads : kScanThreads, SWEEP ? 7 : 4)
+    queue_kernel(RunParams P, uint32_t epoch) {
+    using Smem = typename std::conditional<SWEEP, WarpSmem, WarpStage>::type;
+    __shared__ Smem s_stage[(SWEEP ? kSweepThreads : kScanThreads) / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    WarpStage &stage = s_stage[warp];
+    WarpStage &stage = *reinterpret_cast<WarpStage *>(&s_stage[warp]);
     const unsigned long long cap = P.q->cap;
     unsigned long long my_evals = 0;
 
@@ -847,6 +1064,7 @@ __global__ void __launch_bounds__(kScanThreads, 4) queue_kernel(RunParams P, uin
         const bool wide = (uint64_t)d.m * H * H >= (1ull << 33);
         int nonempty = 0, bk = kNoK;
         uint64_t bg = 0;
+        bool repushed = false;
         if (LEARNED && kind == kGrid) {
             const int ng = min(kMaxGrid, B - A + 1);
             const int gk = lane < ng ? (ng == 1 ? A : A + (int)((int64_t)lane * (B - A) / (ng - 1))) : -1;
@@ -866,8 +1084,18 @@ __global__ void __launch_bounds__(kScanThreads, 4) queue_kernel(RunParams P, uin
             bk = gk >= 0 ? gk : kNoK;
             bg = gk >= 0 ? g : 0;
             warp_best(bk, bg, lo, hi);
+        } else if (SWEEP && kind == kPlain && eff_kpt(P, d, hi - lo) == 0) {
+            if constexpr (SWEEP) {
+                sweep_best(P, d, lo, hi, A, B, *reinterpret_cast<SweepStage *>(&s_stage[warp]), bk, bg, nonempty);
+                my_evals += (unsigned long long)(B - A + 1) * (unsigned long long)nonempty;
+            }
+        } else if (kind == kPlain && nch != seg_chunks(hi - lo, P.min_seg, eff_kpt(P, d, hi - lo))) {
+            // a whole-segment item of a run-sweep series that the sweep cannot take (too many
+            // distinct values, or a wide segment): the segment goes back to the queue as slices
+            push_segment(P, d, it.series, lo, hi, epoch);
+            repushed = true;
         } else if (kind == kPlain) {
-            const int kpt = d.kpt;
+            const int kpt = eff_kpt(P, d, hi - lo);
             const int k0 = A + it.chunk * 32 * kpt;
             const int kmax = min(k0 + 32 * kpt - 1, B);
             if (kpt == 4) {
@@ -889,7 +1117,9 @@ __global__ void __launch_bounds__(kScanThreads, 4) queue_kernel(RunParams P, uin
             my_evals += (unsigned long long)max(0, kmax - kmin + 1) * (unsigned long long)nonempty;
         }
 
-        if (nch == 1 && kind == kPlain) {
+        if (repushed) {
+            // nothing to record: the slices pushed above decide the segment
+        } else if (nch == 1 && kind == kPlain) {
             finish_segment(P, d, it.series, lo, hi, bk, bg, epoch);
         } else {
             // write this member's result over its consumed slot; the last member combines
@@ -1018,16 +1248,28 @@ __global__ void collect_kernel(const SeriesDesc *__restrict__ desc, int64_t S, c
 int queue_grid(int device) {
     int sms = 0, per_sm = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, queue_kernel<true>, kScanThreads, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, queue_kernel<true, false>, kScanThreads, 0) !=
+        cudaSuccess)
+        return 0;
+    return sms * (per_sm > 0 ? per_sm : 1);
+}
+
+int queue_grid_sweep(int device) {
+    int sms = 0, per_sm = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, queue_kernel<false, true>, kSweepThreads, 0) !=
+        cudaSuccess)
         return 0;
     return sms * (per_sm > 0 ? per_sm : 1);
 }
 
 cudaError_t launch_queue_run(const RunParams &P, int grid, uint32_t epoch, cudaStream_t st) {
     if (P.mode == kRunLearned)
-        queue_kernel<true><<<grid, kScanThreads, 0, st>>>(P, epoch);
+        queue_kernel<true, false><<<grid, kScanThreads, 0, st>>>(P, epoch);
+    else if (P.rk)
+        queue_kernel<false, true><<<grid, kSweepThreads, 0, st>>>(P, epoch);
     else
-        queue_kernel<false><<<grid, kScanThreads, 0, st>>>(P, epoch);
+        queue_kernel<false, false><<<grid, kScanThreads, 0, st>>>(P, epoch);
     return cudaGetLastError();
 }
 

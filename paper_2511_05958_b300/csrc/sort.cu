@@ -13,7 +13,9 @@
 // (stable: item-major, then lane order), per-warp digit counts are scanned across warps, the tile is staged in shared memory in sorted order and written out so
 // that consecutive positions of a digit go to consecutive addresses; a running
 // per-digit base carries the order across tiles.  The last step writes the labels
-// in value order to labA and the start of every run of equal values.
+// in value order to labA and the start of every run of equal values.  For series with at
+// most kSweepMaxRuns distinct values a final read writes every sample's run index, in input
+// order, to labB (the scan's run sweep reads it step by step).
 #include "mt4g_internal.cuh"
 
 namespace mt4g {
@@ -229,7 +231,8 @@ __device__ void lsd_passes(SortSmem &sm, int passes, const uint32_t *__restrict_
 __global__ void __launch_bounds__(kSortThreads, 2)
 sort_series_kernel(const uint32_t *__restrict__ samples, SeriesDesc *__restrict__ desc,
                    const int32_t *__restrict__ order, uint32_t *__restrict__ keyA, uint32_t *__restrict__ keyB,
-                   uint16_t *__restrict__ labA, uint16_t *__restrict__ labB, int32_t *__restrict__ runs) {
+                   uint16_t *__restrict__ labA, uint16_t *__restrict__ labB, int32_t *__restrict__ runs,
+                   bool ranks) {
     __shared__ SortSmem sm;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int s = order[blockIdx.x];
@@ -343,6 +346,56 @@ sort_series_kernel(const uint32_t *__restrict__ samples, SeriesDesc *__restrict_
         desc[s].p50 = comp ? k50 >> 16 : k50;
         desc[s].p95 = comp ? k95 >> 16 : k95;
     }
+
+    // ---- run index of every sample in input order (labB), for the run sweep of the scan.
+    // Runs are numbered in value order, so a sample's run index is its rank among the
+    // series' distinct values: a table indexed by value when the value span fits in the
+    // shared memory the passes no longer need, else a binary search over the distinct values.
+    if (ranks && count <= (uint32_t)kSweepMaxRuns) {
+        constexpr uint32_t kLut = (uint32_t)(sizeof(SortSmem) / sizeof(uint16_t));
+        uint16_t *lut = reinterpret_cast<uint16_t *>(&sm);
+        uint32_t *dv = reinterpret_cast<uint32_t *>(&sm);
+        const uint32_t kf = fk[0], kl = fk[N - 1];
+        const uint32_t vmin = comp ? kf >> 16 : kf, vmax = comp ? kl >> 16 : kl;
+        const bool use_lut = vmax - vmin < kLut;
+        for (uint32_t r = tid; r < count; r += kSortThreads) {
+            const uint32_t k2 = fk[rt[r]];
+            const uint32_t v = comp ? k2 >> 16 : k2;
+            if (use_lut)
+                lut[v - vmin] = (uint16_t)r;
+            else
+                dv[r] = v;
+        }
+        __syncthreads();
+        uint16_t *rko = labB + off;
+        for (int b0 = 0; b0 < N; b0 += kSortThreads * kSortItems) {
+            uint32_t v[kSortItems];
+#pragma unroll
+            for (int it = 0; it < kSortItems; it++) {
+                const int i = b0 + it * kSortThreads + tid;
+                v[it] = i < N ? __ldg(in + i) : vmin;
+            }
+#pragma unroll
+            for (int it = 0; it < kSortItems; it++) {
+                const int i = b0 + it * kSortThreads + tid;
+                uint32_t r;
+                if (use_lut) {
+                    r = lut[v[it] - vmin];
+                } else {
+                    uint32_t a = 0, b = count - 1;
+                    while (a < b) {
+                        const uint32_t mid = (a + b) >> 1;
+                        if (dv[mid] < v[it])
+                            a = mid + 1;
+                        else
+                            b = mid;
+                    }
+                    r = a;
+                }
+                if (i < N) rko[i] = (uint16_t)r;
+            }
+        }
+    }
 }
 
 // ---- Eq. 2 reduction (paper Sec. IV-B-1): S_t = sqrt(sum_j (r_tj - min r)^2), then
@@ -447,10 +500,11 @@ cudaError_t launch_check_sort(const SeriesDesc *desc, int64_t S, const uint16_t 
 }
 
 cudaError_t launch_sort(const uint32_t *samples, SeriesDesc *desc, const int32_t *order, int64_t S,
-                        uint32_t *keyA, uint32_t *keyB, uint16_t *labA, uint16_t *labB, int32_t *runs,
+                        uint32_t *keyA, uint32_t *keyB, uint16_t *labA, uint16_t *labB, int32_t *runs, bool ranks,
                         cudaStream_t st) {
     if (S <= 0) return cudaSuccess;
-    sort_series_kernel<<<(unsigned)S, kSortThreads, 0, st>>>(samples, desc, order, keyA, keyB, labA, labB, runs);
+    sort_series_kernel<<<(unsigned)S, kSortThreads, 0, st>>>(samples, desc, order, keyA, keyB, labA, labB, runs,
+                                                             ranks);
     return cudaGetLastError();
 }
 

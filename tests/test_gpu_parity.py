@@ -112,7 +112,7 @@ def test_medium_random_ragged_shapes(eng):
 
 
 def test_every_scan_tile(eng):
-    """Forced scan tiles (32, 64, 128 splits per warp item) give identical results."""
+    """Forced scan tiles (run sweep; 32, 64, 128 splits per warp item) match the oracle."""
     rng = np.random.default_rng(13)
     series = []
     for _ in range(40):
@@ -123,12 +123,50 @@ def test_every_scan_tile(eng):
         series.append(x.astype(np.uint32))
     b = synth.from_arrays(series)
     try:
-        for kpt in (1, 2, 4):
+        for kpt in (mt4g.SCAN_SWEEP, 1, 2, 4):
             eng.set_option(mt4g.OPT_SCAN_KPT, kpt)
             check_scan(eng, b)
             check_segment(eng, b, 1e-3, 2, 16)
     finally:
         eng.set_option(mt4g.OPT_SCAN_KPT, 0)
+
+
+def test_run_sweep_limits_match_slices(eng):
+    """The run sweep at and beyond its limits: 1535, 1536 and 1537 distinct values (odd padding,
+    the cap, and a series sent back to the queue as slices), many distinct values, and a series
+    whose upper segments are too wide for the sweep (m H^2 >= 2^31: slices) while its smaller
+    parts take it.  Every answer equals the 32-split slices'."""
+    rng = np.random.default_rng(29)
+    series = []
+    for U in (1535, 1536, 1537):
+        h = U // 2  # steps 0..59 take values [0, h), steps 60..99 [h, U); every value occurs
+        lo_part = np.concatenate([np.arange(h), rng.integers(0, h, size=60 * 40 - h)])
+        hi_part = np.concatenate([np.arange(h, U), rng.integers(h, U, size=40 * 40 - (U - h))])
+        rng.shuffle(lo_part)
+        rng.shuffle(hi_part)
+        series.append(np.concatenate([lo_part, hi_part]).astype(np.uint32).reshape(100, 40))
+    x = rng.integers(0, 100000, size=(300, 16)).astype(np.uint32)
+    x[120:] += 30000
+    series.append(x)
+    x = rng.integers(0, 200, size=(2048, 2048)).astype(np.uint32)
+    x[700:] += 3
+    x[1500:] += 40
+    series.append(x)
+    series.append(synth.generate(2, 77, 3).series(1))
+    b = synth.from_arrays(series)
+    d = mt4g.to_device_samples(b.samples)
+    out = {}
+    try:
+        for kpt in (mt4g.SCAN_SWEEP, 1):
+            eng.set_option(mt4g.OPT_SCAN_KPT, kpt)
+            r = eng.ks_segment(d, b.offsets, b.steps, 1e-6, 1, 16)
+            sc = eng.ks_scan(d, b.offsets, b.steps)
+            out[kpt] = [t.cpu().numpy() for t in r[1:6]] + [t.cpu().numpy() for t in sc]
+    finally:
+        eng.set_option(mt4g.OPT_SCAN_KPT, 0)
+    for a, c in zip(out[mt4g.SCAN_SWEEP], out[1]):
+        assert np.array_equal(a, c)
+    assert (out[1][0] >= 1).all()
 
 
 def test_edge_values_and_shapes(eng):
