@@ -6,10 +6,12 @@ Workloads (synthetic series from the seeded generator, resident in HBM before ti
   learned (default): 65536 series, T=512 steps, m=128 uint32 samples per step, three change points
       per series (lognormal levels 35/300/800/1100 cycles, 0.5% U{2000..10000} outliers), seed 4;
       17.2 GB per batch.  One step = one learned+exact binary segmentation (alpha 1e-6): per-series
-      radix sort + run table, per-step summaries, the proposal CNN, windows, exact window and grid
-      scans with certification, refinement or full-scan fallback, FP64 p-values.  The plain full
-      exact segmentation of the same batch is timed alongside; every series' answers of the two
-      paths are compared (agreement) and the fallback rate is reported.
+      radix sort + run table, per-step summaries, the proposal CNN, windows; series the run sweep
+      takes (at most 1536 distinct values) are scanned in full by it, the others by exact window
+      and grid scans with certification, refinement or full-scan fallback; FP64 p-values.  The
+      plain full exact segmentation of the same batch is timed alongside; every series' answers
+      of the two paths are compared (agreement) and the fallback rate is reported.  So is the
+      learned path with the sweep off (32-split slices: window and grid probes for every series).
   plain: 1024 series of the same distribution (seed 1), plain full exact segmentation.
   uneven: 16384 series, T ~ U{32..4096}, m in {8,16,64,256}, 0-4 change points with level ratios
       log-uniform in [1.01, 30], 1% Pareto(1.5) tails (seed 2); plain full segmentation, one
@@ -67,7 +69,7 @@ def parse():
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--workload", default="learned", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kpt", type=int, default=0, help="force the scan tile (1, 2, 4); 0 = automatic")
+    ap.add_argument("--kpt", type=int, default=0, help="force the scan tile (1, 2, 4, or 8 for the run sweep); 0 = automatic")
     ap.add_argument("--series", type=int, default=None,
                     help="override the batch size (only for small profiler captures; not a bench value)")
     return ap.parse_args()
@@ -262,6 +264,20 @@ def main():
         for a, c in zip(res_l, out_plain[1:6]):
             same &= (a == c).reshape(S, -1).all(dim=1)
         plain_value = S * world * args.steps / t_plain
+        eng.set_option(mt4g.OPT_SCAN_KPT, 1)  # the probe path on slices, for comparison
+        try:
+            t_sl, out_sl, _, stages_sl, evals_sl, _ = timed(mode, args.steps, 1)
+            stats_sl = eng.learned_stats()
+            same_sl = torch.ones(S, dtype=torch.bool, device=dev)
+            for a, c in zip(res_l, out_sl[1:6]):
+                same_sl &= (a == c).reshape(S, -1).all(dim=1)
+        finally:
+            eng.set_option(mt4g.OPT_SCAN_KPT, 0)
+        line["learned_slices"] = {
+            "value": S * world * args.steps / t_sl, "ms_per_step": t_sl / args.steps * 1e3,
+            "agreement": float(same_sl.float().mean().item()), "evals": evals_sl,
+            "certified_segments": stats_sl["certified"], "refined_segments": stats_sl["refined"],
+            "stage_ms": dict(zip(STAGES, np.asarray(stages_sl).mean(axis=0).tolist()))}
         line.update({"plain_value": plain_value, "plain_ms_per_step": t_plain / args.steps * 1e3,
                      "speedup_vs_plain": value / plain_value, "agreement": float(same.float().mean().item()),
                      "fallback_rate": float(fb.float().mean().item()),

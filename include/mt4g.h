@@ -138,12 +138,14 @@ int mt4g_ks_scan(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets,
  * mode: MT4G_MODE_FULL or MT4G_MODE_REDUCED (as in mt4g_ks_scan), or MT4G_MODE_LEARNED:
  *   the proposal network (weights from mt4g_cnn_load / mt4g_cnn_init; m <= 256) gives
  *   each series windows and a confidence (mt4g_propose).  Series below the confidence
- *   threshold take the full scan.  For the others every segment is first scanned exactly
+ *   threshold take the full scan, and so do series the run sweep takes (MT4G_SCAN_SWEEP):
+ *   its cost per split is below that of the probes.  For the others every segment is first
+ *   scanned exactly
  *   at the windows' splits and at up to 32 grid splits; each gap between grid splits gets
  *   a bound on D from its two end columns, and the gaps whose bound might reach the best
  *   D found are scanned exactly.  The results are therefore those of MT4G_MODE_FULL.
- * fallback: DEVICE int32 [S] or NULL; 1 where the series took the full scan (always 0
- *   outside learned mode).
+ * fallback: DEVICE int32 [S] or NULL; 1 where the series took the full scan (low
+ *   confidence or the run sweep; always 0 outside learned mode).
  */
 int mt4g_ks_segment(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets, const int32_t *steps,
                     int64_t S, double alpha, int32_t min_seg, int32_t max_cp, int32_t mode,

@@ -287,7 +287,7 @@ int make_plan(mt4g_ctx *ctx, const int64_t *offsets, const int32_t *steps, int64
     // for the call when those series carry at least half of the estimated scan cost (T^2 m):
     // the sweep kernel holds fewer warps per SM, which would slow the slices of the others.
     // Series planned for the sweep that turn out to have more distinct values are scanned in
-    // slices by that kernel.  Learned calls keep the slice kernel (their probes are slices).
+    // slices by that kernel.
     {
         const bool forced = ctx->forced_kpt != 0;
         double sw = 0.0, tot = 0.0;
@@ -302,8 +302,7 @@ int make_plan(mt4g_ctx *ctx, const int64_t *offsets, const int32_t *steps, int64
             else
                 sw += cost;
         }
-        P.use_sweep = mode != MT4G_MODE_LEARNED && sw > 0.0 &&
-                      (ctx->forced_kpt == MT4G_SCAN_SWEEP || sw >= 0.5 * tot);
+        P.use_sweep = sw > 0.0 && (ctx->forced_kpt == MT4G_SCAN_SWEEP || sw >= 0.5 * tot);
         if (!P.use_sweep)
             for (auto &d : P.desc)
                 if (d.kpt == 0) d.kpt = 1;

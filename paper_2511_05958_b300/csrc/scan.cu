@@ -32,6 +32,7 @@
 // published or no work is pending, processes it, writes its best split over its slot and
 // counts itself done in the group's counter; the last member combines the group,
 // computes p and, if p <= alpha, records the change point and pushes the children.
+#include <algorithm>
 #include <climits>
 #include <type_traits>
 
@@ -1191,16 +1192,19 @@ __global__ void init_items_kernel(const SeriesDesc *__restrict__ desc, const int
 }
 
 // Learned segmentation: decide each series' path from its proposal confidence (plain scan
-// when conf < conf_min) and push the work for its whole range.
+// when conf < conf_min, or when the run sweep takes the series) and push the work for its
+// whole range.
 __global__ void init_learned_kernel(RunParams P, const float *__restrict__ conf, float conf_min,
                                     int32_t *__restrict__ fallback_out, int64_t S, uint32_t epoch) {
     const int64_t s = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (s >= S) return;
-    if (lane == 0) fallback_out[s] = conf[s] < conf_min ? 1 : 0;
+    const SeriesDesc d = P.desc[s];
+    // the run sweep's cost per split is below the probes': series it takes are scanned in full
+    const bool swept = P.rk != nullptr && d.kpt == 0 && d.nruns <= kSweepMaxRuns;
+    if (lane == 0) fallback_out[s] = (conf[s] < conf_min || swept) ? 1 : 0;
     __syncwarp();
     __threadfence_block();
-    const SeriesDesc d = P.desc[s];
     push_segment(P, d, (int)s, 0, d.T, epoch);
 }
 
@@ -1255,16 +1259,21 @@ int queue_grid(int device) {
 }
 
 int queue_grid_sweep(int device) {
-    int sms = 0, per_sm = 0;
+    int sms = 0, per_sm = 0, per_sm_l = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, queue_kernel<false, true>, kSweepThreads, 0) !=
-        cudaSuccess)
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_l, queue_kernel<true, true>, kSweepThreads, 0) !=
+            cudaSuccess)
         return 0;
+    per_sm = std::min(per_sm, per_sm_l);
     return sms * (per_sm > 0 ? per_sm : 1);
 }
 
 cudaError_t launch_queue_run(const RunParams &P, int grid, uint32_t epoch, cudaStream_t st) {
-    if (P.mode == kRunLearned)
+    if (P.mode == kRunLearned && P.rk)
+        queue_kernel<true, true><<<grid, kSweepThreads, 0, st>>>(P, epoch);
+    else if (P.mode == kRunLearned)
         queue_kernel<true, false><<<grid, kScanThreads, 0, st>>>(P, epoch);
     else if (P.rk)
         queue_kernel<false, true><<<grid, kSweepThreads, 0, st>>>(P, epoch);

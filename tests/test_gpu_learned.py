@@ -232,12 +232,14 @@ def test_learned_mode_equals_full_on_three_level_series(eng, seed):
     b = synth.generate(2, 20 + seed, 256)
     eng.cnn_init(100 + seed)  # untrained: windows are often wrong, certification must catch it
     eng.set_option(mt4g.OPT_CONF_MIN_PPM, 0)  # every series takes the learned path
+    eng.set_option(mt4g.OPT_SCAN_KPT, 1)  # slices: the probes run (the run sweep would take these)
     try:
         full = _segment(eng, b, mt4g.MODE_FULL)
         learned = _segment(eng, b, mt4g.MODE_LEARNED)
         stats = eng.learned_stats()
     finally:
         eng.set_option(mt4g.OPT_CONF_MIN_PPM, 900000)
+        eng.set_option(mt4g.OPT_SCAN_KPT, 0)
     _assert_same(full, learned)
     assert (learned[1][5] == 0).all()  # no fallback at threshold 0
     assert stats["probe_groups"] > 256 and stats["certified"] + stats["refined"] == stats["probe_groups"]
@@ -275,11 +277,17 @@ def test_learned_mode_random_shapes_and_min_seg(eng):
     eng.cnn_init(5)
     eng.set_option(mt4g.OPT_CONF_MIN_PPM, 0)
     try:
-        for alpha, min_seg in [(1e-6, 1), (1e-2, 3), (0.3, 1)]:
-            _assert_same(_segment(eng, b, mt4g.MODE_FULL, alpha, min_seg),
-                         _segment(eng, b, mt4g.MODE_LEARNED, alpha, min_seg))
+        for tile in (1, 0):  # probes on slices; then the default, where the run sweep takes most
+            eng.set_option(mt4g.OPT_SCAN_KPT, tile)
+            for alpha, min_seg in [(1e-6, 1), (1e-2, 3), (0.3, 1)]:
+                full = _segment(eng, b, mt4g.MODE_FULL, alpha, min_seg)
+                rc, res = _segment(eng, b, mt4g.MODE_LEARNED, alpha, min_seg)
+                if tile == 0:
+                    assert res[5].any()  # series the sweep takes are scanned in full
+                _assert_same(full, (rc, res[:5] + [np.zeros_like(res[5])]))
     finally:
         eng.set_option(mt4g.OPT_CONF_MIN_PPM, 900000)
+        eng.set_option(mt4g.OPT_SCAN_KPT, 0)
 
 
 def test_learned_mode_uneven_sample(eng):
@@ -289,9 +297,14 @@ def test_learned_mode_uneven_sample(eng):
     eng.cnn_init(9)
     eng.set_option(mt4g.OPT_CONF_MIN_PPM, 0)
     try:
-        _assert_same(_segment(eng, b, mt4g.MODE_FULL), _segment(eng, b, mt4g.MODE_LEARNED))
+        for tile in (1, mt4g.SCAN_SWEEP):
+            eng.set_option(mt4g.OPT_SCAN_KPT, tile)
+            full = _segment(eng, b, mt4g.MODE_FULL)
+            rc, res = _segment(eng, b, mt4g.MODE_LEARNED)
+            _assert_same(full, (rc, res[:5] + [np.zeros_like(res[5])]))
     finally:
         eng.set_option(mt4g.OPT_CONF_MIN_PPM, 900000)
+        eng.set_option(mt4g.OPT_SCAN_KPT, 0)
 
 
 def test_learned_mode_needs_weights():
@@ -315,6 +328,7 @@ def test_trained_network_gains_over_untrained():
     b = synth.generate(2, 4, 512)
     d = mt4g.to_device_samples(b.samples)
     e = mt4g.Engine(0)
+    e.set_option(mt4g.OPT_SCAN_KPT, 1)  # slices everywhere: the probes run (no run sweep)
     try:
         full = e.ks_segment(d, b.offsets, b.steps, 1e-6, 1, 16, mode=mt4g.MODE_FULL)
         full = [t.cpu().numpy() for t in full[1:6]]
