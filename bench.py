@@ -52,12 +52,12 @@ LAUNCHES = {False: 4, True: 14}  # our kernels per call (plain / learned)
 RECIPES = {2: "synth recipe 2 (T=512, m=128, levels 35/300/800/1100, 0.5% outliers)",
            3: "synth recipe 3 (T 32..4096, m 8..256, 0-4 level ratios 1.01..30, Pareto tails)"}
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch, per series, from the ncu
-# captures summarised in profiles/ (queue_kernel_plain_1024x512x128.md,
-# sort_series_kernel_1024x512x128.md, queue_kernel_learned_2048x512x128.md); keyed by (workload,
-# stage) and scaled by the number of series (the learned capture has 2048 of the 65,536 series).
-# Only workloads whose kernels were captured as they are now appear here; the others report null.
-NCU_TRAFFIC_PER_SERIES = {("plain", "queue"): 480.339456e6 / 1024, ("plain", "sort"): 1363.369472e6 / 1024,
-                          ("learned", "queue"): 2125.035424e6 / 2048}
+# captures summarised in profiles/ (queue_kernel_sweep_512x512x128.md, sort_series_kernel_512x512x128.md,
+# both of 512 series of recipe 2); keyed by (workload, stage) and scaled by the number of series.
+# The learned workload runs the same sort kernel; its queue kernel (learned, with the sweep) was
+# not captured.  Only kernels captured as they are now appear here; the others report null.
+NCU_TRAFFIC_PER_SERIES = {("plain", "queue"): 78.074368e6 / 512, ("plain", "sort"): 858.489344e6 / 512,
+                          ("learned", "sort"): 858.489344e6 / 512}
 STAGES = ["upload", "sort", "proposals", "queue", "collect"]
 
 
@@ -249,13 +249,16 @@ def main():
     clocks = ClockSampler(local)
     t_main, out_main, status, stages, evals, clk = timed(mode, args.steps, args.warmup, clocks)
     stats = eng.learned_stats() if learned else None
+    sweep = eng.last_sweep()
+    ranked = sweep["ranked_samples"]
     value = S * world * args.steps / t_main
     line = {"metric": METRIC, "value": value, "unit": "series/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_main / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32 samples / int32-int64 exact D / f64 p"
             + (" / bf16-fp32 proposal CNN" if learned else ""), "data": "synthetic",
             "config": workload_config(args.workload, world, S), "samples_per_s": value * Ntot / S,
-            "status": int(status), "gpu_launches": LAUNCHES[learned] * args.steps}
+            "status": int(status), "gpu_launches": LAUNCHES[learned] * args.steps,
+            "swept_segments": sweep["swept_segments"], "ranked_samples": ranked}
     if learned:
         res_l = [x.clone() for x in out_main[1:6]]
         fb = out_main[6].clone()
@@ -327,10 +330,11 @@ def main():
                   "peak_source": "measured: mt4g_int32_peak (the scan's 4-op step mix on every SM, this run)",
                   "nominal_peak": nominal_int,
                   "nominal_source": f"{sms} SMs x 128 INT32 lanes x {sm_mhz:.0f} MHz (median SM clock under load)"},
-        "sort": {"kernel": "sort_series_kernel (radix sort + run table)", "bound": "hbm",
-                 "achieved": 10.0 * Ntot / (ms["sort"] / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
-                 "traffic": None,
-                 "algorithmic_units": f"{Ntot} samples x 10 B (4 B read + 6 B sorted value/label written)",
+        "sort": {"kernel": "sort_series_kernel (radix sort + run table + run indices)", "bound": "hbm",
+                 "achieved": (10.0 * Ntot + 6.0 * ranked) / (ms["sort"] / 1e3) / 1e9, "peak": hbm_peak,
+                 "unit": "GB/s", "traffic": None,
+                 "algorithmic_units": f"{Ntot} samples x 10 B (4 B read + 6 B sorted value/label written) + "
+                                      f"{ranked} samples x 6 B (4 B re-read, 2 B run index written)",
                  "peak_source": f"{hbm_src} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
     }
     if learned:

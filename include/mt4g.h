@@ -155,7 +155,7 @@ int mt4g_ks_segment(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offse
 /*
  * mt4g_ks_segment with the samples in HOST memory (the same segmentation and results).
  * The batch is cut into chunks of consecutive series of at most chunk_samples samples each
- * (<= 0: an eighth of the batch, at least 2^24; a longer series is a chunk by itself).  Chunk c + 1 is copied to the device on
+ * (<= 0: an eighth of the batch, at least 2^25; a longer series is a chunk by itself).  Chunk c + 1 is copied to the device on
  * the context's copy stream while chunk c is segmented on cuda_stream, through two device
  * staging buffers the context keeps, so the host-to-device transfer overlaps the computation;
  * give samples_host in page-locked memory (cudaMallocHost / cudaHostRegister) for the copies
@@ -328,6 +328,10 @@ int mt4g_selftest_wait_timeout(mt4g_ctx *ctx, int64_t limit_ns, void *cuda_strea
 /* After mt4g_wait() on a learned call: out[0] = segments decided by their probe group,
  * out[1] = segments that needed refinement slices, out[2] = probe groups pushed. */
 int mt4g_learned_stats(mt4g_ctx *ctx, int64_t *out);
+/* After mt4g_wait(): out[0] = segments the last call scanned by the run sweep
+ * (MT4G_SCAN_SWEEP), out[1] = samples whose run index its sort wrote for the sweep.  No
+ * counterpart in the paper (work accounting for the rooflines). */
+int mt4g_last_sweep(mt4g_ctx *ctx, int64_t *out);
 
 #ifdef __cplusplus
 }

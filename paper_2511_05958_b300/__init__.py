@@ -65,6 +65,7 @@ def load_library():
     L.mt4g_ks_scan.argtypes = [vp, vp, vp, vp, i64, i32, vp, vp, vp, vp, vp]
     L.mt4g_ks_segment.argtypes = [vp, vp, vp, vp, i64, dbl, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp]
     L.mt4g_learned_stats.argtypes = [vp, vp]
+    L.mt4g_last_sweep.argtypes = [vp, vp]
     L.mt4g_ks_scan_noalloc.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp, vp]
     L.mt4g_selftest_wait_timeout.argtypes = [vp, i64, vp]
     L.mt4g_autotune.argtypes = [vp, vp, vp, vp, i64, vp]
@@ -100,7 +101,7 @@ def exported_symbols():
             "mt4g_cnn_load", "mt4g_cnn_forward", "mt4g_cnn_grads", "mt4g_cnn_train_step", "mt4g_propose",
             "mt4g_learned_stats", "mt4g_ks_scan_noalloc", "mt4g_selftest_wait_timeout", "mt4g_critical_value",
             "mt4g_autotune", "mt4g_autotune_save", "mt4g_autotune_load", "mt4g_autotune_get",
-            "mt4g_int32_peak", "mt4g_latency_stats", "mt4g_ks_segment_host"]
+            "mt4g_int32_peak", "mt4g_latency_stats", "mt4g_ks_segment_host", "mt4g_last_sweep"]
 
 
 class ScanResult(NamedTuple):
@@ -197,6 +198,12 @@ class Engine:
         v = np.zeros(3, np.int64)
         self._check(self._L.mt4g_learned_stats(self._h, v.ctypes.data_as(ctypes.c_void_p)))
         return {"certified": int(v[0]), "refined": int(v[1]), "probe_groups": int(v[2])}
+
+    def last_sweep(self) -> dict:
+        """Run-sweep counters of the last call (valid after wait()): segments swept, samples ranked."""
+        v = np.zeros(2, np.int64)
+        self._check(self._L.mt4g_last_sweep(self._h, v.ctypes.data_as(ctypes.c_void_p)))
+        return {"swept_segments": int(v[0]), "ranked_samples": int(v[1])}
 
     def selftest_wait_timeout(self, limit_ns: int = 10_000_000, stream=None) -> int:
         """Run the queue kernel on a queue whose pending item never comes; returns mt4g_wait()'s code."""

@@ -497,8 +497,8 @@ int enqueue_pipeline(mt4g_ctx *ctx, const uint32_t *samples, Plan &P, RunParams 
         CUDA_TRY(ctx, launch_reduce_rank(samples, B.raw_desc, P.S, B.red, B.rank, st));
         sort_in = B.rank;
     }
-    CUDA_TRY(ctx, launch_sort(sort_in, B.desc, B.order, P.S, B.keyA, B.keyB, B.labA, B.labB, B.runs, P.use_sweep,
-                              st));
+    CUDA_TRY(ctx, launch_sort(sort_in, B.desc, B.order, P.S, B.keyA, B.keyB, B.labA, B.labB, B.runs,
+                              P.use_sweep ? &B.q->ranked : nullptr, st));
     if (ctx->checks) CUDA_TRY(ctx, launch_check_sort(B.desc, P.S, B.labA, B.runs, &B.q->status, st));
     mark(ctx, 2, st);
 
@@ -683,6 +683,8 @@ int mt4g_wait(mt4g_ctx *c) {
             sum.certified += h.certified;
             sum.refined += h.refined;
             sum.rec_next += h.rec_next;
+            sum.swept += h.swept;
+            sum.ranked += h.ranked;
         }
         *c->h_hdr = sum;
         c->n_chunk_hdr = 0;
@@ -968,7 +970,7 @@ int mt4g_ks_segment_host(mt4g_ctx *ctx, const uint32_t *samples_host, const int6
     }
     // default: about eight chunks (the first copy and the last chunk's work are not overlapped;
     // much smaller chunks leave the GPU underused), none below 2^24 samples
-    if (chunk_samples <= 0) chunk_samples = std::max<int64_t>((int64_t)1 << 24, (offsets[S] + 7) / 8);
+    if (chunk_samples <= 0) chunk_samples = std::max<int64_t>((int64_t)1 << 25, (offsets[S] + 7) / 8);
     // chunks: consecutive series up to chunk_samples samples (a larger series is a chunk alone)
     std::vector<int64_t> first{0};
     for (int64_t s = 1; s < S; s++)
@@ -1556,6 +1558,13 @@ extern "C" int mt4g_learned_stats(mt4g_ctx *c, int64_t *out) {
     return MT4G_OK;
 }
 
+
+extern "C" int mt4g_last_sweep(mt4g_ctx *c, int64_t *out) {
+    if (!c || !out) return MT4G_EINVAL;
+    out[0] = (int64_t)c->h_hdr->swept;
+    out[1] = (int64_t)c->h_hdr->ranked;
+    return MT4G_OK;
+}
 
 extern "C" int mt4g_selftest_wait_timeout(mt4g_ctx *ctx, int64_t limit_ns, void *cuda_stream) {
     int rc = begin_call(ctx);

@@ -106,6 +106,8 @@ struct QueueHeader {
     unsigned long long rec_cap;
     unsigned long long refined;  // learned segments that needed refinement slices
     unsigned long long certified;  // learned segments decided by their probe group
+    unsigned long long swept;      // segments scanned by the run sweep
+    unsigned long long ranked;     // samples whose run index the sort wrote
 };
 
 enum RunMode : int32_t { kRunScan = 0, kRunSegment = 1, kRunLearned = 2 };
@@ -150,11 +152,11 @@ __host__ __device__ inline int32_t seg_chunks(int32_t H, int32_t min_seg, int32_
 }
 
 // ---- kernels (launch wrappers live in the .cu files) ----
-// ranks: also write every sample's run index to labB for series with at most
-// kSweepMaxRuns distinct values (the run sweep's input).
+// ranked != null: also write every sample's run index to labB for series with at most
+// kSweepMaxRuns distinct values (the run sweep's input), adding their samples to *ranked.
 cudaError_t launch_sort(const uint32_t *samples, SeriesDesc *desc, const int32_t *order, int64_t S,
-                        uint32_t *keyA, uint32_t *keyB, uint16_t *labA, uint16_t *labB, int32_t *runs, bool ranks,
-                        cudaStream_t st);
+                        uint32_t *keyA, uint32_t *keyB, uint16_t *labA, uint16_t *labB, int32_t *runs,
+                        unsigned long long *ranked, cudaStream_t st);
 
 cudaError_t launch_queue_run(const RunParams &P, int grid, uint32_t epoch, cudaStream_t st);
 cudaError_t launch_init_items(const SeriesDesc *desc, const int32_t *qorder, const int64_t *item_base, int64_t S,

@@ -174,7 +174,7 @@ extern "C" int mt4g_ks_scan_noalloc(const uint32_t *samples, const int64_t *offs
                              items, ready, gcount, epoch, st));
     NA_TRY(launch_sort(samples, desc, (const int32_t *)(db + L.off_order), S, (uint32_t *)(db + L.off_keyA),
                        (uint32_t *)(db + L.off_keyB), (uint16_t *)(db + L.off_labA), (uint16_t *)(db + L.off_labB),
-                       (int32_t *)(db + L.off_runs), false, st));
+                       (int32_t *)(db + L.off_runs), nullptr, st));
     RunParams R{};
     R.desc = desc;
     R.lab = (const uint16_t *)(db + L.off_labA);

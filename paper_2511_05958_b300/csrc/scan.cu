@@ -1024,7 +1024,7 @@ __global__ void __launch_bounds__(SWEEP ? kSweepThreads : kScanThreads, SWEEP ? 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     WarpStage &stage = *reinterpret_cast<WarpStage *>(&s_stage[warp]);
     const unsigned long long cap = P.q->cap;
-    unsigned long long my_evals = 0;
+    unsigned long long my_evals = 0, my_swept = 0;
 
     for (;;) {
         unsigned long long ticket = 0;
@@ -1089,6 +1089,7 @@ __global__ void __launch_bounds__(SWEEP ? kSweepThreads : kScanThreads, SWEEP ? 
             if constexpr (SWEEP) {
                 sweep_best(P, d, lo, hi, A, B, *reinterpret_cast<SweepStage *>(&s_stage[warp]), bk, bg, nonempty);
                 my_evals += (unsigned long long)(B - A + 1) * (unsigned long long)nonempty;
+                my_swept++;
             }
         } else if (kind == kPlain && nch != seg_chunks(hi - lo, P.min_seg, eff_kpt(P, d, hi - lo))) {
             // a whole-segment item of a run-sweep series that the sweep cannot take (too many
@@ -1169,6 +1170,7 @@ __global__ void __launch_bounds__(SWEEP ? kSweepThreads : kScanThreads, SWEEP ? 
         __syncwarp();
     }
     if (lane == 0 && my_evals) atomicAdd(&P.q->evals, my_evals);
+    if (lane == 0 && my_swept) atomicAdd(&P.q->swept, my_swept);
 }
 
 // Expand the top-level slices of every series into the queue, costliest series first.

@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(kSortThreads, 2)
 sort_series_kernel(const uint32_t *__restrict__ samples, SeriesDesc *__restrict__ desc,
                    const int32_t *__restrict__ order, uint32_t *__restrict__ keyA, uint32_t *__restrict__ keyB,
                    uint16_t *__restrict__ labA, uint16_t *__restrict__ labB, int32_t *__restrict__ runs,
-                   bool ranks) {
+                   unsigned long long *ranked) {
     __shared__ SortSmem sm;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int s = order[blockIdx.x];
@@ -351,7 +351,8 @@ sort_series_kernel(const uint32_t *__restrict__ samples, SeriesDesc *__restrict_
     // Runs are numbered in value order, so a sample's run index is its rank among the
     // series' distinct values: a table indexed by value when the value span fits in the
     // shared memory the passes no longer need, else a binary search over the distinct values.
-    if (ranks && count <= (uint32_t)kSweepMaxRuns) {
+    if (ranked && count <= (uint32_t)kSweepMaxRuns) {
+        if (tid == 0) atomicAdd(ranked, (unsigned long long)N);
         constexpr uint32_t kLut = (uint32_t)(sizeof(SortSmem) / sizeof(uint16_t));
         uint16_t *lut = reinterpret_cast<uint16_t *>(&sm);
         uint32_t *dv = reinterpret_cast<uint32_t *>(&sm);
@@ -500,11 +501,11 @@ cudaError_t launch_check_sort(const SeriesDesc *desc, int64_t S, const uint16_t 
 }
 
 cudaError_t launch_sort(const uint32_t *samples, SeriesDesc *desc, const int32_t *order, int64_t S,
-                        uint32_t *keyA, uint32_t *keyB, uint16_t *labA, uint16_t *labB, int32_t *runs, bool ranks,
-                        cudaStream_t st) {
+                        uint32_t *keyA, uint32_t *keyB, uint16_t *labA, uint16_t *labB, int32_t *runs,
+                        unsigned long long *ranked, cudaStream_t st) {
     if (S <= 0) return cudaSuccess;
     sort_series_kernel<<<(unsigned)S, kSortThreads, 0, st>>>(samples, desc, order, keyA, keyB, labA, labB, runs,
-                                                             ranks);
+                                                             ranked);
     return cudaGetLastError();
 }
 

@@ -167,3 +167,21 @@ def test_consistency_checks_pass_and_change_nothing(eng):
         eng.set_option(mt4g.OPT_CHECKS, 0)
         _, ref2 = _seg(eng, d, b)
         _same(ref2, [t.cpu().numpy() for t in r2[1:6]])
+
+
+def test_sweep_counters(eng):
+    """mt4g_last_sweep: a plain call on series the run sweep takes ranks every sample and sweeps
+    segments; with the sweep off (32-split slices) both counters are zero and answers agree."""
+    b = synth.generate(2, 61, 24)
+    d = mt4g.to_device_samples(b.samples)
+    _, ref = _seg(eng, d, b)
+    c = eng.last_sweep()
+    assert c["ranked_samples"] == int(b.offsets[-1]) and c["swept_segments"] >= 24
+    eng.set_option(mt4g.OPT_SCAN_KPT, 1)
+    try:
+        _, sl = _seg(eng, d, b)
+        c1 = eng.last_sweep()
+    finally:
+        eng.set_option(mt4g.OPT_SCAN_KPT, 0)
+    assert c1 == {"swept_segments": 0, "ranked_samples": 0}
+    _same(ref, sl)
