@@ -605,7 +605,7 @@ __device__ __forceinline__ void lc_add(SweepStage &ss, uint32_t idx, uint32_t w,
     if (act) atomicAdd(&ss.lc[idx].x, w);
 }
 
-constexpr int kSweepPre = 8;  // run indices of one step held per lane (steps of up to 256 samples)
+constexpr int kSweepPre = 4;  // run indices of one step held per lane (the first 128 samples)
 
 // Run indices of step t into registers: slot q holds sample lane + 32 q.
 __device__ __forceinline__ void sweep_load_step(const uint16_t *__restrict__ rk, int64_t t, int m, int lane,
@@ -614,12 +614,13 @@ __device__ __forceinline__ void sweep_load_step(const uint16_t *__restrict__ rk,
 #pragma unroll
     for (int q = 0; q < kSweepPre; q++) {
         const int j = lane + 32 * q;
-        buf[q] = j < m ? (uint32_t)__ldg(src + j) : 0u;
+        buf[q] = 0u;
+        if (32 * q < m && j < m) buf[q] = (uint32_t)__ldg(src + j);
     }
 }
 
 // Move the samples of step t to the left part: l grows by H at each sample's run.  `buf`
-// holds the step's first 256 run indices (sweep_load_step); the rest are read here.
+// holds the step's first 128 run indices (sweep_load_step); the rest are read here.
 __device__ __forceinline__ void sweep_apply_step(SweepStage &ss, const uint16_t *__restrict__ rk, int64_t t, int m,
                                                  uint32_t H, int lane, const uint32_t (&buf)[kSweepPre]) {
 #pragma unroll
@@ -734,8 +735,8 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
             const int32_t v0 = (int32_t)(hc + na * q.y);
             hc += q.z;
             const int32_t v1 = (int32_t)(hc + na * q.w);
-            mx = max(mx, max(v0, v1));
-            mn = min(mn, min(v0, v1));
+            mx = __vimax3_s32(mx, v0, v1);
+            mn = __vimin3_s32(mn, v0, v1);
         }
         const uint32_t blk = hc - h0;  // sum of l over the block
         // every lane has read l for split k: step k's samples move left now (reductions the warp
