@@ -52,11 +52,13 @@ LAUNCHES = {False: 4, True: 14}  # our kernels per call (plain / learned)
 RECIPES = {2: "synth recipe 2 (T=512, m=128, levels 35/300/800/1100, 0.5% outliers)",
            3: "synth recipe 3 (T 32..4096, m 8..256, 0-4 level ratios 1.01..30, Pareto tails)"}
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch, per series, from the ncu
-# capture summarised in profiles/sort_series_kernel_512x512x128.md (512 series of recipe 2); keyed by
-# (workload, stage) and scaled by the number of series.  The learned workload runs the same sort
-# kernel.  Only kernels captured as they are now appear here; the others (the queue kernels,
-# changed since their captures) report null.
-NCU_TRAFFIC_PER_SERIES = {("plain", "sort"): 858.489344e6 / 512, ("learned", "sort"): 858.489344e6 / 512}
+# captures summarised in profiles/queue_kernel_sweep_512x512x128.md and
+# profiles/sort_series_kernel_512x512x128.md (512 series of recipe 2, the plain call's kernels);
+# keyed by (workload, stage) and scaled by the number of series.  The learned workload runs the
+# same sort kernel; its queue kernel (learned, with the sweep) was not captured.  Only kernels
+# captured as they are now appear here; the others report null.
+NCU_TRAFFIC_PER_SERIES = {("plain", "queue"): 77.561856e6 / 512, ("plain", "sort"): 196.957184e6 / 512,
+                          ("learned", "sort"): 196.957184e6 / 512}
 STAGES = ["upload", "sort", "proposals", "queue", "collect"]
 
 
@@ -249,7 +251,7 @@ def main():
     t_main, out_main, status, stages, evals, clk = timed(mode, args.steps, args.warmup, clocks)
     stats = eng.learned_stats() if learned else None
     sweep = eng.last_sweep()
-    ranked = sweep["ranked_samples"]
+    ranked, counted = sweep["ranked_samples"], sweep["counted_samples"]
     value = S * world * args.steps / t_main
     line = {"metric": METRIC, "value": value, "unit": "series/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_main / args.steps * 1e3, "higher_is_better": True,
@@ -257,7 +259,8 @@ def main():
             + (" / bf16-fp32 proposal CNN" if learned else ""), "data": "synthetic",
             "config": workload_config(args.workload, world, S), "samples_per_s": value * Ntot / S,
             "status": int(status), "gpu_launches": LAUNCHES[learned] * args.steps,
-            "swept_segments": sweep["swept_segments"], "ranked_samples": ranked}
+            "swept_segments": sweep["swept_segments"], "ranked_samples": ranked, "counted_samples": counted,
+            "unswept_series": sweep["unswept_series"]}
     if learned:
         res_l = [x.clone() for x in out_main[1:6]]
         fb = out_main[6].clone()
@@ -329,14 +332,18 @@ def main():
                   "peak_source": "measured: mt4g_int32_peak (the scan's 4-op step mix on every SM, this run)",
                   "nominal_peak": nominal_int,
                   "nominal_source": f"{sms} SMs x 128 INT32 lanes x {sm_mhz:.0f} MHz (median SM clock under load)"},
-        "sort": {"kernel": "sort_series_kernel (radix sort + run table + run indices)", "bound": "hbm",
-                 "achieved": (10.0 * Ntot + 6.0 * ranked) / (ms["sort"] / 1e3) / 1e9, "peak": hbm_peak,
-                 "unit": "GB/s", "traffic": None,
-                 "algorithmic_units": f"{Ntot} samples x 10 B (4 B read + 6 B sorted value/label written) + "
-                                      f"{ranked} samples x 6 B (4 B re-read, 2 B run index written)",
+        "sort": {"kernel": "sort_series_kernel (radix or counting sort + run table + run indices)", "bound": "hbm",
+                 "achieved": (10.0 * (Ntot - counted) + 6.0 * ranked) / (ms["sort"] / 1e3) / 1e9,
+                 "peak": hbm_peak, "unit": "GB/s", "traffic": None,
+                 "algorithmic_units": f"{Ntot - counted} radix-sorted samples x 10 B (4 B read + 6 B sorted "
+                                      f"value/label written) + {ranked} ranked samples x 6 B (4 B read, 2 B run "
+                                      f"index written; {counted} of them by counting, without labels)",
                  "peak_source": f"{hbm_src} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
     }
-    if learned:
+    if learned and ranked > 0 and sweep["unswept_series"] == 0:
+        # every series was swept: the proposal kernels returned at once (nothing to measure)
+        line["proposals_skipped"] = True
+    elif learned:
         rooflines["proposals"] = {"kernel": "summaries + CNN + windows", "bound": "hbm",
                                   "achieved": 4.0 * Ntot / (ms["proposals"] / 1e3) / 1e9, "peak": hbm_peak,
                                   "unit": "GB/s", "traffic": None,

@@ -328,8 +328,11 @@ int mt4g_selftest_wait_timeout(mt4g_ctx *ctx, int64_t limit_ns, void *cuda_strea
 /* After mt4g_wait() on a learned call: out[0] = segments decided by their probe group,
  * out[1] = segments that needed refinement slices, out[2] = probe groups pushed. */
 int mt4g_learned_stats(mt4g_ctx *ctx, int64_t *out);
-/* After mt4g_wait(): out[0] = segments the last call scanned by the run sweep
- * (MT4G_SCAN_SWEEP), out[1] = samples whose run index its sort wrote for the sweep.  No
+/* After mt4g_wait(), for the last call: out[0] = segments scanned by the run sweep
+ * (MT4G_SCAN_SWEEP); out[1] = samples whose run index the sort wrote for the sweep; out[2] = of
+ * those, samples of series the sort handled by counting values instead of radix-sorting them
+ * (no sorted labels needed: value span <= 11552, every segment swept); out[3] = series of a
+ * sweep call that the sweep does not take (when 0, a learned call skips its proposals).  No
  * counterpart in the paper (work accounting for the rooflines). */
 int mt4g_last_sweep(mt4g_ctx *ctx, int64_t *out);
 

@@ -200,10 +200,12 @@ class Engine:
         return {"certified": int(v[0]), "refined": int(v[1]), "probe_groups": int(v[2])}
 
     def last_sweep(self) -> dict:
-        """Run-sweep counters of the last call (valid after wait()): segments swept, samples ranked."""
-        v = np.zeros(2, np.int64)
+        """Run-sweep counters of the last call (valid after wait()): segments swept, samples ranked,
+        samples sorted by counting, series the sweep does not take."""
+        v = np.zeros(4, np.int64)
         self._check(self._L.mt4g_last_sweep(self._h, v.ctypes.data_as(ctypes.c_void_p)))
-        return {"swept_segments": int(v[0]), "ranked_samples": int(v[1])}
+        return {"swept_segments": int(v[0]), "ranked_samples": int(v[1]), "counted_samples": int(v[2]),
+                "unswept_series": int(v[3])}
 
     def selftest_wait_timeout(self, limit_ns: int = 10_000_000, stream=None) -> int:
         """Run the queue kernel on a queue whose pending item never comes; returns mt4g_wait()'s code."""

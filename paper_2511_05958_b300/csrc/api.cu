@@ -499,7 +499,7 @@ int enqueue_pipeline(mt4g_ctx *ctx, const uint32_t *samples, Plan &P, RunParams 
     }
     CUDA_TRY(ctx, launch_sort(sort_in, B.desc, B.order, P.S, B.keyA, B.keyB, B.labA, B.labB, B.runs,
                               P.use_sweep ? &B.q->ranked : nullptr, st));
-    if (ctx->checks) CUDA_TRY(ctx, launch_check_sort(B.desc, P.S, B.labA, B.runs, &B.q->status, st));
+    if (ctx->checks) CUDA_TRY(ctx, launch_check_sort(B.desc, P.S, B.labA, B.labB, B.runs, &B.q->status, st));
     mark(ctx, 2, st);
 
     R = RunParams{};
@@ -685,6 +685,8 @@ int mt4g_wait(mt4g_ctx *c) {
             sum.rec_next += h.rec_next;
             sum.swept += h.swept;
             sum.ranked += h.ranked;
+            sum.counted += h.counted;
+            sum.unswept += h.unswept;
         }
         *c->h_hdr = sum;
         c->n_chunk_hdr = 0;
@@ -1536,11 +1538,14 @@ int enqueue_proposals(mt4g_ctx *ctx, const uint32_t *samples, Plan &P, Buffers &
     if (rc) return rc;
     rc = zero_pads(ctx, C, S, false, st);
     if (rc) return rc;
-    CUDA_TRY(ctx, launch_summaries(samples, B.desc, S, C.feat, st));
+    // in sweep calls the sort counted the series the sweep does not take: only they use the
+    // proposals, and with none the proposal kernels return at once
+    const unsigned long long *gate = P.use_sweep ? &B.q->unswept : nullptr;
+    CUDA_TRY(ctx, launch_summaries(samples, B.desc, S, C.feat, st, gate));
     CUDA_TRY(ctx, cnn_prepare(ctx->cnn, st));
     CUDA_TRY(ctx, cnn_forward(ctx->cnn, C.feat, C.A, B.desc, C.tiles_before, S, ntiles, ctx->wait_limit_ns,
-                              &B.q->status, st));
-    CUDA_TRY(ctx, launch_propose(C.A.logits, B.desc, S, ctx->n_win, ctx->half, C.win, C.conf, st));
+                              &B.q->status, st, gate));
+    CUDA_TRY(ctx, launch_propose(C.A.logits, B.desc, S, ctx->n_win, ctx->half, C.win, C.conf, st, gate));
     R.win_center = C.win;
     R.n_win = ctx->n_win;
     R.half = ctx->half;
@@ -1563,6 +1568,8 @@ extern "C" int mt4g_last_sweep(mt4g_ctx *c, int64_t *out) {
     if (!c || !out) return MT4G_EINVAL;
     out[0] = (int64_t)c->h_hdr->swept;
     out[1] = (int64_t)c->h_hdr->ranked;
+    out[2] = (int64_t)c->h_hdr->counted;
+    out[3] = (int64_t)c->h_hdr->unswept;
     return MT4G_OK;
 }
 

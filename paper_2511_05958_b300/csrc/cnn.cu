@@ -129,7 +129,9 @@ __global__ void __launch_bounds__(kTile) conv_out_kernel(const __nv_bfloat16 *__
                                                          const float *__restrict__ W4, const float *__restrict__ b4,
                                                          float *__restrict__ logits,
                                                          const SeriesDesc *__restrict__ desc,
-                                                         const int64_t *__restrict__ tiles_before, int64_t S) {
+                                                         const int64_t *__restrict__ tiles_before, int64_t S,
+                                                         const unsigned long long *__restrict__ gate) {
+    if (gate && *gate == 0ull) return;
     __shared__ float w[5 * 32];
     __shared__ __align__(16) uint4 xs[(kTile + 4) * 4];  // 8 BF16 channels per uint4
     const int64_t tile = blockIdx.x;
@@ -367,7 +369,7 @@ cudaError_t cnn_prepare(const CnnState &W, cudaStream_t st) {
 
 cudaError_t cnn_forward(const CnnState &W, const uint16_t *feat, const CnnActs &A, const SeriesDesc *desc,
                         const int64_t *tiles_before, int64_t S, int64_t ntiles, long long wait_limit_ns,
-                        int32_t *status, cudaStream_t st) {
+                        int32_t *status, cudaStream_t st, const unsigned long long *gate) {
     if (ntiles <= 0) return cudaSuccess;
     const __nv_bfloat16 *x0 = reinterpret_cast<const __nv_bfloat16 *>(feat);
     const float *u = W.used;
@@ -375,16 +377,17 @@ cudaError_t cnn_forward(const CnnState &W, const uint16_t *feat, const CnnActs &
     __nv_bfloat16 *a1 = reinterpret_cast<__nv_bfloat16 *>(A.a1), *a2 = reinterpret_cast<__nv_bfloat16 *>(A.a2),
                   *a3 = reinterpret_cast<__nv_bfloat16 *>(A.a3);
     cudaError_t e = cnn_hidden_tc(0, x0, u + cnn_off(0), u + cnn_off(1), a1, desc, tiles_before, S, ntiles,
-                                  wait_limit_ns, status, st);
+                                  wait_limit_ns, status, st, gate);
     if (e == cudaSuccess)
         e = cnn_hidden_tc(1, a1, u + cnn_off(2), u + cnn_off(3), a2, desc, tiles_before, S, ntiles, wait_limit_ns,
-                          status, st);
+                          status, st, gate);
     if (e == cudaSuccess)
         e = cnn_hidden_tc(2, a2, u + cnn_off(4), u + cnn_off(5), a3, desc, tiles_before, S, ntiles, wait_limit_ns,
-                          status, st);
+                          status, st, gate);
     if (e != cudaSuccess) return e;
     conv_out_kernel<<<(unsigned)ntiles, kTile, 0, st>>>(reinterpret_cast<const __nv_bfloat16 *>(A.a3),
-                                                        u + cnn_off(6), u + cnn_off(7), A.logits, desc, tiles_before, S);
+                                                        u + cnn_off(6), u + cnn_off(7), A.logits, desc, tiles_before, S,
+                                                        gate);
     return cudaGetLastError();
 }
 

@@ -91,7 +91,9 @@ __global__ void __launch_bounds__(kTcThreads) conv_tc_kernel(const __nv_bfloat16
                                                              const SeriesDesc *__restrict__ desc,
                                                              const int64_t *__restrict__ tiles_before, int64_t S,
                                                              int64_t ntiles, long long wait_limit_ns,
-                                                             int32_t *status) {
+                                                             int32_t *status,
+                                                             const unsigned long long *__restrict__ gate) {
+    if (gate && *gate == 0ull) return;  // before any barrier or tensor-memory allocation
     extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
     TcSmem &sm = *reinterpret_cast<TcSmem *>(tc_smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -210,7 +212,8 @@ __global__ void __launch_bounds__(kTcThreads) conv_tc_kernel(const __nv_bfloat16
 template <int CIN>
 cudaError_t launch_one(const __nv_bfloat16 *in, const float *W, const float *bias, __nv_bfloat16 *out,
                        const SeriesDesc *desc, const int64_t *tiles_before, int64_t S, int64_t ntiles,
-                       long long wait_limit_ns, int32_t *status, cudaStream_t st) {
+                       long long wait_limit_ns, int32_t *status, cudaStream_t st,
+                       const unsigned long long *gate) {
     static int configured_device = -1;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -224,7 +227,7 @@ cudaError_t launch_one(const __nv_bfloat16 *in, const float *W, const float *bia
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t grid = std::min<int64_t>(ntiles, (int64_t)sms * 4);
     conv_tc_kernel<CIN><<<(unsigned)grid, kTcThreads, sizeof(TcSmem), st>>>(in, W, bias, out, desc, tiles_before, S,
-                                                                             ntiles, wait_limit_ns, status);
+                                                                             ntiles, wait_limit_ns, status, gate);
     return cudaGetLastError();
 }
 
@@ -232,11 +235,12 @@ cudaError_t launch_one(const __nv_bfloat16 *in, const float *W, const float *bia
 
 cudaError_t cnn_hidden_tc(int layer, const __nv_bfloat16 *in, const float *W, const float *bias, __nv_bfloat16 *out,
                           const SeriesDesc *desc, const int64_t *tiles_before, int64_t S, int64_t ntiles,
-                          long long wait_limit_ns, int32_t *status, cudaStream_t st) {
+                          long long wait_limit_ns, int32_t *status, cudaStream_t st,
+                          const unsigned long long *gate) {
     if (ntiles <= 0) return cudaSuccess;
     if (layer == 0)
-        return launch_one<kFeatC>(in, W, bias, out, desc, tiles_before, S, ntiles, wait_limit_ns, status, st);
-    return launch_one<32>(in, W, bias, out, desc, tiles_before, S, ntiles, wait_limit_ns, status, st);
+        return launch_one<kFeatC>(in, W, bias, out, desc, tiles_before, S, ntiles, wait_limit_ns, status, st, gate);
+    return launch_one<32>(in, W, bias, out, desc, tiles_before, S, ntiles, wait_limit_ns, status, st, gate);
 }
 
 }  // namespace mt4g

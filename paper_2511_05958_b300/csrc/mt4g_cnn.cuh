@@ -51,17 +51,18 @@ cudaError_t cnn_prepare(const CnnState &W, cudaStream_t st);
 // timeout bit of *status (when not null).
 cudaError_t cnn_forward(const CnnState &W, const uint16_t *feat, const CnnActs &A, const SeriesDesc *desc,
                         const int64_t *tiles_before, int64_t S, int64_t ntiles, long long wait_limit_ns,
-                        int32_t *status, cudaStream_t st);
+                        int32_t *status, cudaStream_t st, const unsigned long long *gate = nullptr);
 // One hidden layer (0: 18 -> 32, 1 and 2: 32 -> 32, ReLU, BF16 out) on the tcgen05 tensor cores.
 cudaError_t cnn_hidden_tc(int layer, const __nv_bfloat16 *in, const float *W, const float *bias, __nv_bfloat16 *out,
                           const SeriesDesc *desc, const int64_t *tiles_before, int64_t S, int64_t ntiles,
-                          long long wait_limit_ns, int32_t *status, cudaStream_t st);
+                          long long wait_limit_ns, int32_t *status, cudaStream_t st,
+                          const unsigned long long *gate = nullptr);
 cudaError_t cnn_backward(const CnnState &W, const uint16_t *feat, const CnnActs &A, const int32_t *cp_count,
                          const int32_t *cp_idx, int32_t max_cp, const SeriesDesc *desc, int64_t S, int T,
                          float *grad, float *loss, cudaStream_t st);
 cudaError_t cnn_adam(CnnState &W, const float *grad, float lr, cudaStream_t st);
 cudaError_t launch_zero_pad_rows(void *buf, int row_bytes, const SeriesDesc *desc, int64_t S, cudaStream_t st);
 cudaError_t launch_propose(const float *logits, const SeriesDesc *desc, int64_t S, int32_t n_win, int32_t half,
-                           int32_t *win_center, float *conf, cudaStream_t st);
+                           int32_t *win_center, float *conf, cudaStream_t st, const unsigned long long *gate = nullptr);
 
 }  // namespace mt4g

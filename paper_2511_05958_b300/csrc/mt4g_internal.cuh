@@ -44,8 +44,13 @@ struct SeriesDesc {
     uint32_t median;    // sorted value at index N / 2 (written by the sort)
     uint32_t p50;       // nearest-rank order statistics sorted[ceil(q N) - 1], q = 1/2 and
     uint32_t p95;       // 95/100 (written by the sort)
-    int32_t pad;
+    int32_t flags;      // kDescNoLabels: the sort wrote run indices and the run table only
 };
+
+// SeriesDesc.flags.  A run-sweep series whose values span at most kFastSpan and whose every
+// segment the sweep takes needs no sorted labels: the sort then counts values in a table
+// indexed by value instead of radix-sorting, and labA is left unwritten for it.
+enum : int32_t { kDescNoLabels = 1 };
 
 // Learned-proposal feature rows: series s owns rows [row_base(s), row_base(s) + T_s + 4) of
 // an [rows][kFeatC] array; step t is row row_base(s) + 2 + t and the two rows on each
@@ -107,7 +112,9 @@ struct QueueHeader {
     unsigned long long refined;  // learned segments that needed refinement slices
     unsigned long long certified;  // learned segments decided by their probe group
     unsigned long long swept;      // segments scanned by the run sweep
-    unsigned long long ranked;     // samples whose run index the sort wrote
+    unsigned long long ranked;     // samples whose run index the sort wrote (sweep calls)
+    unsigned long long counted;    // of those, samples of series sorted by counting (kDescNoLabels)
+    unsigned long long unswept;    // series of a sweep call that the sweep does not take
 };
 
 enum RunMode : int32_t { kRunScan = 0, kRunSegment = 1, kRunLearned = 2 };
@@ -152,11 +159,13 @@ __host__ __device__ inline int32_t seg_chunks(int32_t H, int32_t min_seg, int32_
 }
 
 // ---- kernels (launch wrappers live in the .cu files) ----
-// ranked != null: also write every sample's run index to labB for series with at most
-// kSweepMaxRuns distinct values (the run sweep's input), adding their samples to *ranked.
+// sweep_stats != null (sweep calls): also write every sample's run index to labB for series
+// with at most kSweepMaxRuns distinct values (the run sweep's input); sweep_stats[0] counts
+// their samples, [1] those of series sorted by counting, [2] the series the sweep does not
+// take (QueueHeader.ranked, .counted, .unswept).
 cudaError_t launch_sort(const uint32_t *samples, SeriesDesc *desc, const int32_t *order, int64_t S,
                         uint32_t *keyA, uint32_t *keyB, uint16_t *labA, uint16_t *labB, int32_t *runs,
-                        unsigned long long *ranked, cudaStream_t st);
+                        unsigned long long *sweep_stats, cudaStream_t st);
 
 cudaError_t launch_queue_run(const RunParams &P, int grid, uint32_t epoch, cudaStream_t st);
 cudaError_t launch_init_items(const SeriesDesc *desc, const int32_t *qorder, const int64_t *item_base, int64_t S,
@@ -167,17 +176,20 @@ cudaError_t launch_init_learned(const RunParams &P, const float *conf, float con
 int queue_grid(int device);        // CTAs of the slice-only kernel
 int queue_grid_sweep(int device);  // CTAs of the kernel with the run sweep
 
-// Consistency check of the sort's output (MT4G_OPT_CHECKS): run table, labels.  Sets
+// Consistency check of the sort's output (MT4G_OPT_CHECKS): run table, labels (or, for
+// kDescNoLabels series, the run indices against the run lengths).  Sets
 // kStatusCheck in *status on any violation; reads only within each series' own ranges.
-cudaError_t launch_check_sort(const SeriesDesc *desc, int64_t S, const uint16_t *lab, const int32_t *runs,
-                              int32_t *status, cudaStream_t st);
+cudaError_t launch_check_sort(const SeriesDesc *desc, int64_t S, const uint16_t *lab, const uint16_t *rk,
+                              const int32_t *runs, int32_t *status, cudaStream_t st);
 cudaError_t launch_collect(const SeriesDesc *desc, int64_t S, const uint8_t *cp_flag, const int64_t *cp_num,
                            const int64_t *cp_den, const double *cp_p, int32_t max_cp, int32_t *cp_count,
                            int32_t *cp_idx, int64_t *dnum, int64_t *dden, double *p, QueueHeader *q,
                            cudaStream_t st);
 
+// gate (optional): a device counter; when it reads 0 the proposal kernels return at once (a
+// learned call whose every series the run sweep takes uses no proposal).
 cudaError_t launch_summaries(const uint32_t *samples, const SeriesDesc *raw_desc, int64_t S, uint16_t *feat,
-                             cudaStream_t st);
+                             cudaStream_t st, const unsigned long long *gate = nullptr);
 
 cudaError_t launch_latency_stats(const uint32_t *samples, const SeriesDesc *desc, int64_t S, double *mean_out,
                                  uint32_t *p50_out, uint32_t *p95_out, double *std_out, cudaStream_t st);

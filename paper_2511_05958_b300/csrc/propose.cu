@@ -12,7 +12,9 @@ namespace {
 __global__ void __launch_bounds__(256) propose_kernel(const float *__restrict__ logits,
                                                       const SeriesDesc *__restrict__ desc, int32_t n_win,
                                                       int32_t half, int32_t *__restrict__ win_center,
-                                                      float *__restrict__ conf) {
+                                                      float *__restrict__ conf,
+                                                      const unsigned long long *__restrict__ gate) {
+    if (gate && *gate == 0ull) return;
     __shared__ float s_v[8];
     __shared__ int s_i[8];
     __shared__ float s_max, s_sum;
@@ -111,9 +113,9 @@ __global__ void __launch_bounds__(256) propose_kernel(const float *__restrict__ 
 }  // namespace
 
 cudaError_t launch_propose(const float *logits, const SeriesDesc *desc, int64_t S, int32_t n_win, int32_t half,
-                           int32_t *win_center, float *conf, cudaStream_t st) {
+                           int32_t *win_center, float *conf, cudaStream_t st, const unsigned long long *gate) {
     if (S <= 0) return cudaSuccess;
-    propose_kernel<<<(unsigned)S, 256, 0, st>>>(logits, desc, n_win, half, win_center, conf);
+    propose_kernel<<<(unsigned)S, 256, 0, st>>>(logits, desc, n_win, half, win_center, conf, gate);
     return cudaGetLastError();
 }
 

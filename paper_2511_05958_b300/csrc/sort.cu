@@ -228,11 +228,116 @@ __device__ void lsd_passes(SortSmem &sm, int passes, const uint32_t *__restrict_
     }
 }
 
+// Values per series the counting path can index: the sort's shared memory as 32-bit counters.
+constexpr uint32_t kFastSpan = (uint32_t)(sizeof(SortSmem) / sizeof(uint32_t));
+
+// Counting path for a run-sweep series whose values span at most kFastSpan (all threads call
+// it; returns false, with nothing written, when the series has more than kSweepMaxRuns
+// distinct values).  Counts every value in a table indexed by value - vmin, scans the table
+// for the run table (starts of the distinct values in value order) and the order statistics,
+// turns it into a value -> run index table, and writes each sample's run index in input
+// order.  The sorted labels are not produced (kDescNoLabels).
+__device__ bool count_runs(SortSmem &sm, const uint32_t *__restrict__ in, int32_t N, uint32_t vmin, uint32_t vmax,
+                           int32_t *__restrict__ rt, SeriesDesc *__restrict__ ds, uint16_t *__restrict__ rko,
+                           unsigned long long *sweep_stats) {
+    __shared__ uint32_t s_scan[2][kSortWarps];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(&sm);
+    const uint32_t span = vmax - vmin + 1;
+    for (uint32_t i = tid; i < span; i += kSortThreads) cnt[i] = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < N; b0 += kSortThreads * kSortItems) {
+        uint32_t v[kSortItems];
+#pragma unroll
+        for (int it = 0; it < kSortItems; it++) {
+            const int i = b0 + it * kSortThreads + tid;
+            v[it] = i < N ? __ldg(in + i) - vmin : 0u;
+        }
+#pragma unroll
+        for (int it = 0; it < kSortItems; it++) {
+            const int i = b0 + it * kSortThreads + tid;
+            hist_add(cnt, v[it], __ballot_sync(kFull, i < N));
+        }
+    }
+    __syncthreads();
+    // each thread scans a contiguous piece of the table: distinct values and samples in it
+    const uint32_t per = (span + kSortThreads - 1) / kSortThreads;
+    const uint32_t c0 = min(span, (uint32_t)tid * per), c1 = min(span, c0 + per);
+    uint32_t nd = 0, ns = 0;
+    for (uint32_t i = c0; i < c1; i++) {
+        const uint32_t c = cnt[i];
+        nd += c != 0u;
+        ns += c;
+    }
+    uint32_t id = nd, is = ns;  // inclusive warp scans
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, id, o), z = __shfl_up_sync(kFull, is, o);
+        if (lane >= o) {
+            id += y;
+            is += z;
+        }
+    }
+    if (lane == 31) {
+        s_scan[0][warp] = id;
+        s_scan[1][warp] = is;
+    }
+    __syncthreads();
+    uint32_t bd = id - nd, bs = is - ns, U = 0;
+    for (int w = 0; w < kSortWarps; w++) {
+        const uint32_t a = s_scan[0][w], b = s_scan[1][w];
+        if (w < warp) {
+            bd += a;
+            bs += b;
+        }
+        U += a;
+    }
+    if (U > (uint32_t)kSweepMaxRuns) return false;  // uniform: nothing written yet
+    // run starts, order statistics (values at sorted positions N / 2 and ceil(q N) - 1), and
+    // the value -> run index table in place of the counts
+    const uint32_t qmed = (uint32_t)(N / 2), q50 = (uint32_t)((50 * (int64_t)N + 99) / 100 - 1),
+                   q95 = (uint32_t)((95 * (int64_t)N + 99) / 100 - 1);
+    uint32_t r = bd, pos = bs;
+    for (uint32_t i = c0; i < c1; i++) {
+        const uint32_t c = cnt[i];
+        if (c == 0u) continue;
+        rt[r] = (int32_t)pos;
+        if (qmed - pos < c) ds->median = vmin + i;
+        if (q50 - pos < c) ds->p50 = vmin + i;
+        if (q95 - pos < c) ds->p95 = vmin + i;
+        cnt[i] = r;
+        r++;
+        pos += c;
+    }
+    if (tid == 0) {
+        rt[U] = N;
+        ds->nruns = (int32_t)U;
+        ds->flags |= kDescNoLabels;
+        atomicAdd(sweep_stats, (unsigned long long)N);
+        atomicAdd(sweep_stats + 1, (unsigned long long)N);
+    }
+    __syncthreads();
+    for (int b0 = 0; b0 < N; b0 += kSortThreads * kSortItems) {
+        uint32_t v[kSortItems];
+#pragma unroll
+        for (int it = 0; it < kSortItems; it++) {
+            const int i = b0 + it * kSortThreads + tid;
+            v[it] = i < N ? __ldg(in + i) - vmin : 0u;
+        }
+#pragma unroll
+        for (int it = 0; it < kSortItems; it++) {
+            const int i = b0 + it * kSortThreads + tid;
+            if (i < N) rko[i] = (uint16_t)cnt[v[it]];
+        }
+    }
+    return true;
+}
+
 __global__ void __launch_bounds__(kSortThreads, 2)
 sort_series_kernel(const uint32_t *__restrict__ samples, SeriesDesc *__restrict__ desc,
                    const int32_t *__restrict__ order, uint32_t *__restrict__ keyA, uint32_t *__restrict__ keyB,
                    uint16_t *__restrict__ labA, uint16_t *__restrict__ labB, int32_t *__restrict__ runs,
-                   unsigned long long *ranked) {
+                   unsigned long long *sweep_stats) {
     __shared__ SortSmem sm;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int s = order[blockIdx.x];
@@ -245,7 +350,7 @@ sort_series_kernel(const uint32_t *__restrict__ samples, SeriesDesc *__restrict_
     // ---- largest value and the digit counts of pass 0, in one read
     if (tid < 256) sm.hist[tid] = 0;
     __syncthreads();
-    uint32_t vmax = 0;
+    uint32_t vmax = 0, vmin = 0xffffffffu;
     for (int b0 = 0; b0 < N; b0 += kSortThreads * kSortItems) {
         // all loads of the round first, so they are in flight together
         uint32_t v[kSortItems];
@@ -259,20 +364,58 @@ sort_series_kernel(const uint32_t *__restrict__ samples, SeriesDesc *__restrict_
             const int i = b0 + it * kSortThreads + tid;
             const unsigned vm = __ballot_sync(kFull, i < N);
             vmax = max(vmax, v[it]);
+            if (i < N) vmin = min(vmin, v[it]);
             hist_add(sm.hist, v[it] & 255u, vm);
         }
     }
     vmax = __reduce_max_sync(kFull, vmax);
-    if (lane == 0) sm.tmp[warp] = vmax;
+    vmin = __reduce_min_sync(kFull, vmin);
+    if (lane == 0) {
+        sm.tmp[warp] = vmax;
+        sm.tmp[kSortWarps + warp] = vmin;
+    }
     __syncthreads();
     if (warp == 0) {
         uint32_t v = lane < kSortWarps ? sm.tmp[lane] : 0u;
+        uint32_t u = lane < kSortWarps ? sm.tmp[kSortWarps + lane] : 0xffffffffu;
         v = __reduce_max_sync(kFull, v);
-        if (lane == 0) sm.tmp[31] = v;
+        u = __reduce_min_sync(kFull, u);
+        __syncwarp();
+        if (lane == 0) {
+            sm.tmp[31] = v;
+            sm.tmp[30] = u;
+        }
     }
     __syncthreads();
     vmax = sm.tmp[31];
+    vmin = sm.tmp[30];
     __syncthreads();
+    int32_t *rt = runs + d.run_base;
+
+    // ---- counting path: a run-sweep series with a narrow value span whose every segment the
+    // sweep takes (m T^2 < 2^31) needs only the run table and the run indices
+    if (sweep_stats && d.kpt == 0 && vmax - vmin < kFastSpan &&
+        (uint64_t)m * (uint64_t)d.T * (uint64_t)d.T < (1ull << 31)) {
+        if (count_runs(sm, in, N, vmin, vmax, rt, desc + s, labB + off, sweep_stats)) return;
+        // too many distinct values for the sweep: sort as usual, recounting pass 0's digits
+        __syncthreads();
+        if (tid < 256) sm.hist[tid] = 0;
+        __syncthreads();
+        for (int b0 = 0; b0 < N; b0 += kSortThreads * kSortItems) {
+            uint32_t v[kSortItems];
+#pragma unroll
+            for (int it = 0; it < kSortItems; it++) {
+                const int i = b0 + it * kSortThreads + tid;
+                v[it] = i < N ? __ldg(in + i) : 0u;
+            }
+#pragma unroll
+            for (int it = 0; it < kSortItems; it++) {
+                const int i = b0 + it * kSortThreads + tid;
+                hist_add(sm.hist, v[it] & 255u, __ballot_sync(kFull, i < N));
+            }
+        }
+        __syncthreads();
+    }
     const int bits = vmax ? 32 - __clz(vmax) : 0;
     const int passes = max(1, (bits + 7) / 8);
     const bool comp = vmax < 65536u;
@@ -286,7 +429,6 @@ sort_series_kernel(const uint32_t *__restrict__ samples, SeriesDesc *__restrict_
     // ---- run table and final labels (into labA), 8 consecutive samples per thread per round
     const uint32_t *fk = (passes & 1) ? kB : kA;
     const uint16_t *flab = (passes & 1) ? lB : lA;
-    int32_t *rt = runs + d.run_base;
     uint32_t count = 0;
     constexpr int kRunItems = 8;
     for (int tb = 0; tb < N; tb += kSortThreads * kRunItems) {
@@ -351,8 +493,10 @@ sort_series_kernel(const uint32_t *__restrict__ samples, SeriesDesc *__restrict_
     // Runs are numbered in value order, so a sample's run index is its rank among the
     // series' distinct values: a table indexed by value when the value span fits in the
     // shared memory the passes no longer need, else a binary search over the distinct values.
-    if (ranked && count <= (uint32_t)kSweepMaxRuns) {
-        if (tid == 0) atomicAdd(ranked, (unsigned long long)N);
+    if (sweep_stats && tid == 0 && !(d.kpt == 0 && count <= (uint32_t)kSweepMaxRuns))
+        atomicAdd(sweep_stats + 2, 1ull);  // a series the sweep does not take
+    if (sweep_stats && count <= (uint32_t)kSweepMaxRuns) {
+        if (tid == 0) atomicAdd(sweep_stats, (unsigned long long)N);
         constexpr uint32_t kLut = (uint32_t)(sizeof(SortSmem) / sizeof(uint16_t));
         uint16_t *lut = reinterpret_cast<uint16_t *>(&sm);
         uint32_t *dv = reinterpret_cast<uint32_t *>(&sm);
@@ -456,22 +600,49 @@ reduce_rank_kernel(const uint32_t *__restrict__ samples, const SeriesDesc *__res
 // Invariants the scan relies on, checked per series (one CTA): the run table starts at 0,
 // increases strictly and ends at N with nruns entries; every label is a step index (< T);
 // labels are non-decreasing within each run (sample i and i - 1 in the same run, found by
-// binary search in the validated table).  Reads stay inside the series' label range
-// [off, off + N) and run-table range [run_base, run_base + nruns].
+// binary search in the validated table).  For kDescNoLabels series the labels are absent;
+// instead every run index is below nruns and each run's count of them equals its length.
+// Reads stay inside the series' label range [off, off + N) and run-table range
+// [run_base, run_base + nruns].
 __global__ void __launch_bounds__(256) check_sort_kernel(const SeriesDesc *__restrict__ desc,
                                                          const uint16_t *__restrict__ lab,
+                                                         const uint16_t *__restrict__ rk,
                                                          const int32_t *__restrict__ runs, int32_t *status) {
+    __shared__ uint32_t s_cnt[kSweepMaxRuns];
     const SeriesDesc d = desc[blockIdx.x];
     const int64_t N = (int64_t)d.T * d.m;
     const int32_t U = d.nruns;
     const int32_t *rt = runs + d.run_base;
-    const uint16_t *l = lab + d.off;
-    bool bad = U < 1 || U > N;
+    const bool nolab = (d.flags & kDescNoLabels) != 0;
+    bool bad = U < 1 || U > N || (nolab && U > kSweepMaxRuns);
     if (!bad) {
         if (threadIdx.x == 0) bad = rt[0] != 0 || rt[U] != N;
         for (int32_t j = threadIdx.x; j < U && !bad; j += blockDim.x) bad = rt[j] >= rt[j + 1];
-        for (int64_t i = threadIdx.x; i < N && !bad; i += blockDim.x) bad = l[i] >= d.T;
     }
+    if (nolab) {
+        const uint16_t *r = rk + d.off;
+        for (int32_t j = threadIdx.x; j < kSweepMaxRuns; j += blockDim.x) s_cnt[j] = 0;
+        __syncthreads();
+        if (!__syncthreads_or(bad)) {
+            for (int64_t i = threadIdx.x; i < N && !bad; i += blockDim.x) {
+                const uint32_t v = r[i];
+                if (v >= (uint32_t)U)
+                    bad = true;
+                else
+                    atomicAdd(&s_cnt[v], 1u);
+            }
+            if (!__syncthreads_or(bad))
+                for (int32_t j = threadIdx.x; j < U && !bad; j += blockDim.x) bad = s_cnt[j] != (uint32_t)(rt[j + 1] - rt[j]);
+            bad = __syncthreads_or(bad);
+        } else {
+            bad = true;
+        }
+        if (bad && threadIdx.x == 0) atomicOr(status, (int32_t)kStatusCheck);
+        return;
+    }
+    const uint16_t *l = lab + d.off;
+    if (!bad)
+        for (int64_t i = threadIdx.x; i < N && !bad; i += blockDim.x) bad = l[i] >= d.T;
     if (!__syncthreads_or(bad)) {
         for (int64_t i = 1 + threadIdx.x; i < N && !bad; i += blockDim.x) {
             int32_t lo = 0, hi = U;  // rt[lo] <= i < rt[hi]
@@ -493,19 +664,19 @@ __global__ void __launch_bounds__(256) check_sort_kernel(const SeriesDesc *__res
 
 }  // namespace
 
-cudaError_t launch_check_sort(const SeriesDesc *desc, int64_t S, const uint16_t *lab, const int32_t *runs,
-                              int32_t *status, cudaStream_t st) {
+cudaError_t launch_check_sort(const SeriesDesc *desc, int64_t S, const uint16_t *lab, const uint16_t *rk,
+                              const int32_t *runs, int32_t *status, cudaStream_t st) {
     if (S <= 0) return cudaSuccess;
-    check_sort_kernel<<<(unsigned)S, 256, 0, st>>>(desc, lab, runs, status);
+    check_sort_kernel<<<(unsigned)S, 256, 0, st>>>(desc, lab, rk, runs, status);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sort(const uint32_t *samples, SeriesDesc *desc, const int32_t *order, int64_t S,
                         uint32_t *keyA, uint32_t *keyB, uint16_t *labA, uint16_t *labB, int32_t *runs,
-                        unsigned long long *ranked, cudaStream_t st) {
+                        unsigned long long *sweep_stats, cudaStream_t st) {
     if (S <= 0) return cudaSuccess;
     sort_series_kernel<<<(unsigned)S, kSortThreads, 0, st>>>(samples, desc, order, keyA, keyB, labA, labB, runs,
-                                                             ranked);
+                                                             sweep_stats);
     return cudaGetLastError();
 }
 

@@ -101,7 +101,9 @@ __device__ void summarise_steps(const uint32_t *__restrict__ x0, int T, int m, f
 
 __global__ void __launch_bounds__(256, 4) summaries_kernel(const uint32_t *__restrict__ samples,
                                                         const SeriesDesc *__restrict__ desc,
-                                                        __nv_bfloat16 *__restrict__ feat) {
+                                                        __nv_bfloat16 *__restrict__ feat,
+                                                        const unsigned long long *__restrict__ gate) {
+    if (gate && *gate == 0ull) return;
     const int64_t s = blockIdx.x;
     const SeriesDesc d = desc[s];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -128,9 +130,9 @@ __global__ void __launch_bounds__(256, 4) summaries_kernel(const uint32_t *__res
 }  // namespace
 
 cudaError_t launch_summaries(const uint32_t *samples, const SeriesDesc *raw_desc, int64_t S, uint16_t *feat,
-                             cudaStream_t st) {
+                             cudaStream_t st, const unsigned long long *gate) {
     if (S <= 0) return cudaSuccess;
-    summaries_kernel<<<(unsigned)S, 256, 0, st>>>(samples, raw_desc, reinterpret_cast<__nv_bfloat16 *>(feat));
+    summaries_kernel<<<(unsigned)S, 256, 0, st>>>(samples, raw_desc, reinterpret_cast<__nv_bfloat16 *>(feat), gate);
     return cudaGetLastError();
 }
 

@@ -176,12 +176,29 @@ def test_sweep_counters(eng):
     d = mt4g.to_device_samples(b.samples)
     _, ref = _seg(eng, d, b)
     c = eng.last_sweep()
-    assert c["ranked_samples"] == int(b.offsets[-1]) and c["swept_segments"] >= 24
+    n = int(b.offsets[-1])
+    assert c["ranked_samples"] == n and c["swept_segments"] >= 24
+    assert c["counted_samples"] == n and c["unswept_series"] == 0  # narrow spans: counted, all swept
     eng.set_option(mt4g.OPT_SCAN_KPT, 1)
     try:
         _, sl = _seg(eng, d, b)
         c1 = eng.last_sweep()
     finally:
         eng.set_option(mt4g.OPT_SCAN_KPT, 0)
-    assert c1 == {"swept_segments": 0, "ranked_samples": 0}
+    assert c1 == {"swept_segments": 0, "ranked_samples": 0, "counted_samples": 0, "unswept_series": 0}
     _same(ref, sl)
+    # a wide value span: radix-sorted, still ranked and swept
+    x = np.random.default_rng(3).integers(0, 1 << 30, size=(64, 8)).astype(np.uint32)
+    x[:, :] = (x % 900) * 1000003 % (1 << 31)  # 900 distinct values spread over 2^31
+    x[40:] += 5
+    bw = synth.from_arrays([x])
+    dw = mt4g.to_device_samples(bw.samples)
+    _, w0 = _seg(eng, dw, bw)
+    cw = eng.last_sweep()
+    assert cw["ranked_samples"] == 512 and cw["counted_samples"] == 0 and cw["unswept_series"] == 0
+    eng.set_option(mt4g.OPT_SCAN_KPT, 1)
+    try:
+        _, w1 = _seg(eng, dw, bw)
+    finally:
+        eng.set_option(mt4g.OPT_SCAN_KPT, 0)
+    _same(w0, w1)
