@@ -580,9 +580,14 @@ __device__ __forceinline__ void warp_best(int &bk, uint64_t &bg, int lo, int hi)
 // g_k.  The sweep takes segments with m H^2 < 2^31, where every quantity above is an exact
 // 32-bit integer.
 struct __align__(16) SweepStage {
-    uint2 lc[kSweepMaxRuns];      // (l, C) of compact run c; during setup .x counts run r
+    uint32_t l[kSweepMaxRuns];    // l of compact run c; during setup the count of run r, then C_c
     uint16_t map[kSweepMaxRuns];  // run -> compact run
 };
+
+// Largest lane block: ceil(kSweepMaxRuns / 32) made even and, from 8 on, 2 mod 4.  Each lane
+// keeps its block's C_c in registers (they do not change during a segment's sweep).
+constexpr int kSweepMaxR = 50;
+static_assert(kSweepMaxRuns <= 32 * 48, "lane blocks above kSweepMaxR runs");
 
 union __align__(16) WarpSmem {
     WarpStage ws;
@@ -599,10 +604,10 @@ __device__ __forceinline__ int eff_kpt(const RunParams &P, const SeriesDesc &d, 
     return d.kpt ? d.kpt : (sweepable(P, d, H) ? 0 : 1);
 }
 
-// lc[idx].x += w for every active lane.  A shared-memory reduction without return: the warp
+// l[idx] += w for every active lane.  A shared-memory reduction without return: the warp
 // does not wait for it, and lanes that hit the same run are serialised by the hardware.
 __device__ __forceinline__ void lc_add(SweepStage &ss, uint32_t idx, uint32_t w, bool act) {
-    if (act) atomicAdd(&ss.lc[idx].x, w);
+    if (act) atomicAdd(&ss.l[idx], w);
 }
 
 constexpr int kSweepPre = 4;  // run indices of one step held per lane (the first 128 samples)
@@ -647,12 +652,12 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
     const uint32_t H = (uint32_t)(hi - lo);
     const unsigned lt = lanemask_lt();
 
-    // in-segment samples per run, into lc[r].x
+    // in-segment samples per run, into l[r]
     if (lo == 0 && hi == d.T) {
         const int32_t *rt = P.runs + d.run_base;
-        for (int r = lane; r < U; r += 32) ss.lc[r].x = (uint32_t)(__ldg(rt + r + 1) - __ldg(rt + r));
+        for (int r = lane; r < U; r += 32) ss.l[r] = (uint32_t)(__ldg(rt + r + 1) - __ldg(rt + r));
     } else {
-        for (int r = lane; r < U; r += 32) ss.lc[r].x = 0;
+        for (int r = lane; r < U; r += 32) ss.l[r] = 0;
         __syncwarp();
         const int64_t e1 = (int64_t)hi * m;
         for (int64_t e0 = (int64_t)lo * m; e0 < e1; e0 += 512) {  // 16 loads in flight per lane
@@ -672,7 +677,7 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
     uint32_t nc = 0, cs = 0;  // runs kept so far, in-segment samples so far
     for (int r0 = 0; r0 < U; r0 += 32) {
         const int r = r0 + lane;
-        const uint32_t n = r < U ? ss.lc[r].x : 0u;
+        const uint32_t n = r < U ? ss.l[r] : 0u;
         const unsigned keep = __ballot_sync(kFull, n != 0);
         uint32_t incl = n;
 #pragma unroll
@@ -684,7 +689,7 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
         if (n != 0) {
             const uint32_t ci = nc + (uint32_t)__popc(keep & lt);
             ss.map[r] = (uint16_t)ci;
-            ss.lc[ci] = make_uint2(0u, cs + incl);
+            ss.l[ci] = cs + incl;  // C of compact run ci, until the lanes have read it
         }
         nc += (uint32_t)__popc(keep);
         cs += __shfl_sync(kFull, incl, 31);
@@ -695,7 +700,7 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
     // an odd count is padded with a copy of the last run (l = 0, same C): it repeats the
     // last value and changes no maximum, and lets every block read whole pairs
     const int Ue = Uc + (Uc & 1);
-    if ((Uc & 1) && lane == 0) ss.lc[Uc] = make_uint2(0u, cs);
+    if ((Uc & 1) && lane == 0) ss.l[Uc] = cs;
     // blocks: R runs per lane, R even; R = 2 mod 4 for larger R keeps the 16-byte pair loads of
     // a quarter warp on distinct banks
     int R = (Ue + 31) / 32;
@@ -703,9 +708,18 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
     if (R >= 8 && (R & 3) == 0) R += 2;
     const int b0 = min(lane * R, Ue), b1 = min(b0 + R, Ue);
     const int npair = (b1 - b0) >> 1;
-    const uint4 *pairs = reinterpret_cast<const uint4 *>(&ss.lc[b0]);
+    const uint2 *pairs = reinterpret_cast<const uint2 *>(&ss.l[b0]);
     __syncwarp();
-    const uint32_t Cb = b0 > 0 ? ss.lc[b0 - 1].y : 0u;  // in-segment samples below the block
+    const uint32_t Cb = b0 > 0 ? ss.l[b0 - 1] : 0u;  // in-segment samples below the block
+    // C of the block's runs; past the block's end the last run's C, so that a pair evaluated
+    // there with l = 0 repeats the last value and changes neither max nor min
+    const uint32_t Clast = b1 > b0 ? ss.l[b1 - 1] : 0u;
+    uint32_t Cr[kSweepMaxR];
+#pragma unroll
+    for (int j = 0; j < kSweepMaxR; j++) Cr[j] = b0 + j < b1 ? ss.l[b0 + j] : Clast;
+    __syncwarp();
+    for (int c = lane; c < Ue; c += 32) ss.l[c] = 0u;
+    __syncwarp();
 
     for (int t = lo; t < A; t++) {
         uint32_t buf[kSweepPre];
@@ -728,15 +742,28 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
         const uint32_t h0 = a * Cb;
         uint32_t hc = h0;
         int32_t mx = INT_MIN, mn = INT_MAX;
-#pragma unroll 4
-        for (int j = 0; j < npair; j++) {
-            const uint4 q = pairs[j];
-            hc += q.x;
-            const int32_t v0 = (int32_t)(hc + na * q.y);
-            hc += q.z;
-            const int32_t v1 = (int32_t)(hc + na * q.w);
-            mx = __vimax3_s32(mx, v0, v1);
-            mn = __vimin3_s32(mn, v0, v1);
+        // groups of 4 pairs, loads first; pairs past the block read as l = 0 (see Cr)
+#pragma unroll
+        for (int g = 0; g < (kSweepMaxR / 2 + 3) / 4; g++) {
+            if (4 * g >= npair) break;
+            uint2 q[4];
+#pragma unroll
+            for (int t = 0; t < 4; t++) {
+                const int j = 4 * g + t;
+                q[t] = (j < kSweepMaxR / 2 && j < npair) ? pairs[j] : make_uint2(0u, 0u);
+            }
+#pragma unroll
+            for (int t = 0; t < 4; t++) {
+                const int j = 4 * g + t;
+                if (j < kSweepMaxR / 2) {
+                    hc += q[t].x;
+                    const int32_t v0 = (int32_t)(hc + na * Cr[2 * j]);
+                    hc += q[t].y;
+                    const int32_t v1 = (int32_t)(hc + na * Cr[2 * j + 1]);
+                    mx = __vimax3_s32(mx, v0, v1);
+                    mn = __vimin3_s32(mn, v0, v1);
+                }
+            }
         }
         const uint32_t blk = hc - h0;  // sum of l over the block
         // every lane has read l for split k: step k's samples move left now (reductions the warp
@@ -1018,7 +1045,7 @@ __device__ void slice_best(const RunParams &P, const SeriesDesc &d, int lo, int 
 // up to kSweepMaxRuns runs), launched as CTAs of kSweepThreads; without it, the smaller
 // slice staging allows more resident warps.
 template <bool LEARNED, bool SWEEP>
-__global__ void __launch_bounds__(SWEEP ? kSweepThreads : kScanThreads, SWEEP ? 7 : 4)
+__global__ void __launch_bounds__(SWEEP ? kSweepThreads : kScanThreads, SWEEP ? 8 : 4)
     queue_kernel(RunParams P, uint32_t epoch) {
     using Smem = typename std::conditional<SWEEP, WarpSmem, WarpStage>::type;
     __shared__ Smem s_stage[(SWEEP ? kSweepThreads : kScanThreads) / 32];
