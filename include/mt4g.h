@@ -139,8 +139,9 @@ int mt4g_ks_scan(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets,
  *   the proposal network (weights from mt4g_cnn_load / mt4g_cnn_init; m <= 256) gives
  *   each series windows and a confidence (mt4g_propose).  Series below the confidence
  *   threshold take the full scan, and so do series the run sweep takes (MT4G_SCAN_SWEEP):
- *   its cost per split is below that of the probes.  For the others every segment is first
- *   scanned exactly
+ *   its cost per split is below that of the probes; when it takes every series of the call,
+ *   the proposal kernels return at once (no windows are computed).  For the others every
+ *   segment is first scanned exactly
  *   at the windows' splits and at up to 32 grid splits; each gap between grid splits gets
  *   a bound on D from its two end columns, and the gaps whose bound might reach the best
  *   D found are scanned exactly.  The results are therefore those of MT4G_MODE_FULL.
