@@ -289,7 +289,6 @@ def main():
                      "plain_stage_ms": dict(zip(STAGES, np.asarray(stages_p).mean(axis=0).tolist()))})
 
     # ---------------- end to end through host buffers (pinned), copies in the timed region
-    d2h = S * 4 + S * MAX_CP * (4 + 8 + 8 + 8) + (S * 4 if learned else 0)
     h2d = b.samples.nbytes + b.offsets.nbytes + b.steps.nbytes
     e_steps = max(1, min(args.steps, 5))
     barrier()
@@ -306,6 +305,7 @@ def main():
     f1.record(stream)
     barrier()
     te = max_over_ranks(f0.elapsed_time(f1) / 1e3)
+    d2h = sum(x.numel() * x.element_size() for x in outs_h)  # every result tensor read back per step
     line["e2e"] = {"value": S * world * e_steps / te, "unit": "series/s", "h2d_bytes_per_step": int(h2d),
                    "d2h_bytes_per_step": int(d2h), "steps": e_steps}
 

@@ -65,9 +65,10 @@ extern "C" {
 /* Scan tile value of the run sweep: one warp walks all splits of a segment in order, moving
    one step's samples to the left part at a time.  It applies to series with at most 1536
    distinct values and to segments with m H^2 < 2^31; other segments of such series are
-   scanned in 32-split slices.  Where the autotuner has no entry, full and reduced calls plan
-   it for series of at most 2^17 samples and use it when those carry at least half of the
-   call's T^2 m; learned calls scan in slices. */
+   scanned in 32-split slices.  Where the autotuner has no entry, every call (full, reduced or
+   learned) plans it for series of at most 2^17 samples and uses it when those carry at least
+   half of the call's T^2 m.  In learned calls the series the sweep takes are scanned in full
+   by it (see mt4g_ks_segment); the proposal probes serve the series scanned in slices. */
 #define MT4G_SCAN_SWEEP 8
 #define MT4G_MAX_SERIES_SAMPLES (1LL << 30)
 
@@ -147,11 +148,18 @@ int mt4g_ks_scan(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets,
  *   D found are scanned exactly.  The results are therefore those of MT4G_MODE_FULL.
  * fallback: DEVICE int32 [S] or NULL; 1 where the series took the full scan (low
  *   confidence or the run sweep; always 0 outside learned mode).
+ * crit: DEVICE double [S * max_cp] or NULL; beside each reported change point, the critical
+ *   value of D at level alpha for the two sample sizes of the split that created it (Eq. 1,
+ *   read with the minus sign its printed radicand lost and the natural log):
+ *     crit = sqrt(-1/2 ln(alpha / 2) (n_L + n_R) / (n_L n_R)),
+ *   n_L = m (k - lo), n_R = m (hi - k) (m = 1 in MT4G_MODE_REDUCED), evaluated in FP64 in that
+ *   order with ln(alpha / 2) taken once on the host; the paper reports this threshold as the
+ *   confidence of a boundary (Sec. IV-B-1 (4)).  Unused slots are 0.
  */
 int mt4g_ks_segment(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets, const int32_t *steps,
                     int64_t S, double alpha, int32_t min_seg, int32_t max_cp, int32_t mode,
                     int32_t *cp_count, int32_t *cp_idx, int64_t *dnum, int64_t *dden, double *p,
-                    int32_t *fallback, void *cuda_stream);
+                    int32_t *fallback, double *crit, void *cuda_stream);
 
 /*
  * mt4g_ks_segment with the samples in HOST memory (the same segmentation and results).
@@ -169,7 +177,7 @@ int mt4g_ks_segment(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offse
 int mt4g_ks_segment_host(mt4g_ctx *ctx, const uint32_t *samples_host, const int64_t *offsets, const int32_t *steps,
                          int64_t S, double alpha, int32_t min_seg, int32_t max_cp, int32_t mode,
                          int64_t chunk_samples, int32_t *cp_count, int32_t *cp_idx, int64_t *dnum, int64_t *dden,
-                         double *p, int32_t *fallback, void *cuda_stream);
+                         double *p, int32_t *fallback, double *crit, void *cuda_stream);
 
 /* ------------------------------------------------------------------ learned proposal
  *
@@ -279,20 +287,19 @@ int mt4g_latency_stats(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *of
  * Allocation-free variant of mt4g_ks_scan (no counterpart in the paper).
  *
  * For callers that cannot allocate device (or host) memory: code running inside a memory
- * pool or arena it does not own, callers in the middle of a stream capture, or processes
- * that forbid allocation after start-up.  Same arguments and results as mt4g_ks_scan in
- * MT4G_MODE_FULL (top-level test over every split of every series), but without a context:
- * all scratch comes from one static device array of MT4G_NOALLOC_SCRATCH_BYTES that every
- * GPU loading this library holds until the process exits, and host tables from a static
- * host buffer.  Limits: S <= MT4G_NOALLOC_MAX_SERIES, total samples <=
- * MT4G_NOALLOC_MAX_SAMPLES, total steps <= MT4G_NOALLOC_MAX_STEPS; beyond them the call
- * returns MT4G_EINVAL before touching the GPU.  It runs on the current CUDA device.
- * The array keeps the last call's contents and is shared by all calls on a device: the
- * call clears what must start at zero, but calls whose GPU work overlaps (different
+ * pool or arena it does not own, or processes that forbid allocation after start-up.  Same
+ * arguments and results as mt4g_ks_scan in MT4G_MODE_FULL (top-level test over every split
+ * of every series), but without a context: all scratch comes from one static device array
+ * of MT4G_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until the process
+ * exits, and host tables from a static host buffer.  Limits: S <= MT4G_NOALLOC_MAX_SERIES,
+ * total samples <= MT4G_NOALLOC_MAX_SAMPLES, total steps <= MT4G_NOALLOC_MAX_STEPS; beyond
+ * them the call returns MT4G_EINVAL before touching the GPU.  It runs on the current CUDA
+ * device.  The array keeps the last call's contents and is shared by all calls on a device:
+ * the call clears what must start at zero, but calls whose GPU work overlaps (different
  * streams or host threads) race on it.  The first call on a device looks up the array's
- * address (cudaGetSymbolAddress), so make that first call before any stream capture.  The
- * call is synchronous: it returns after the outputs are written, with MT4G_OK,
- * MT4G_EINVAL, MT4G_ECUDA, MT4G_ETIMEOUT or MT4G_ECAPACITY.
+ * address (cudaGetSymbolAddress).  The call is synchronous: it returns after the outputs are
+ * written (or, on a failed enqueue, after the work already enqueued has finished), with
+ * MT4G_OK, MT4G_EINVAL, MT4G_ECUDA, MT4G_ETIMEOUT or MT4G_ECAPACITY.
  */
 #define MT4G_NOALLOC_SCRATCH_BYTES (12u << 20)
 #define MT4G_NOALLOC_MAX_SERIES 4096

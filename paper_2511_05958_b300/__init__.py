@@ -63,7 +63,7 @@ def load_library():
     L.mt4g_wait.argtypes = [vp]
     L.mt4g_set_option.argtypes = [vp, ctypes.c_int, i64]
     L.mt4g_ks_scan.argtypes = [vp, vp, vp, vp, i64, i32, vp, vp, vp, vp, vp]
-    L.mt4g_ks_segment.argtypes = [vp, vp, vp, vp, i64, dbl, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp]
+    L.mt4g_ks_segment.argtypes = [vp, vp, vp, vp, i64, dbl, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
     L.mt4g_learned_stats.argtypes = [vp, vp]
     L.mt4g_last_sweep.argtypes = [vp, vp]
     L.mt4g_ks_scan_noalloc.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp, vp]
@@ -77,7 +77,8 @@ def load_library():
     L.mt4g_stage_times.argtypes = [vp, vp, i32]
     L.mt4g_int32_peak.argtypes = [ctypes.c_int, vp]
     L.mt4g_latency_stats.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp, vp, vp]
-    L.mt4g_ks_segment_host.argtypes = [vp, vp, vp, vp, i64, dbl, i32, i32, i32, i64, vp, vp, vp, vp, vp, vp, vp]
+    L.mt4g_ks_segment_host.argtypes = [vp, vp, vp, vp, i64, dbl, i32, i32, i32, i64, vp, vp, vp, vp, vp, vp, vp,
+                                       vp]
     L.mt4g_last_work.argtypes = [vp, vp]
     L.mt4g_summaries.argtypes = [vp, vp, vp, vp, i64, vp, vp]
     L.mt4g_cnn_init.argtypes = [vp, ctypes.c_uint64]
@@ -119,6 +120,7 @@ class SegmentResult(NamedTuple):
     dden: "torch.Tensor"
     p: "torch.Tensor"
     fallback: "torch.Tensor"  # [S], 1 where a learned call took the full scan
+    crit: "torch.Tensor"      # [S, max_cp], Eq. 1 critical value of each change point's split
 
 
 def _host_tables(offsets, steps):
@@ -267,12 +269,14 @@ class Engine:
                                 torch.empty((S, max_cp), dtype=torch.int64, device=dev),
                                 torch.empty((S, max_cp), dtype=torch.int64, device=dev),
                                 torch.empty((S, max_cp), dtype=torch.float64, device=dev),
-                                torch.empty(S, dtype=torch.int32, device=dev))
+                                torch.empty(S, dtype=torch.int32, device=dev),
+                                torch.empty((S, max_cp), dtype=torch.float64, device=dev))
         rc = self._L.mt4g_ks_segment(self._h, _dev_ptr(samples, "samples"), offsets.ctypes.data_as(ctypes.c_void_p),
                                      steps.ctypes.data_as(ctypes.c_void_p), S, float(alpha), int(min_seg),
                                      int(max_cp), mode, _dev_ptr(out.count, "count"), _dev_ptr(out.idx, "idx"),
                                      _dev_ptr(out.dnum, "dnum"), _dev_ptr(out.dden, "dden"), _dev_ptr(out.p, "p"),
-                                     _dev_ptr(out.fallback, "fallback"), _stream_handle(stream))
+                                     _dev_ptr(out.fallback, "fallback"), _dev_ptr(out.crit, "crit"),
+                                     _stream_handle(stream))
         self._check(rc)
         status = OK
         if sync:
@@ -305,13 +309,15 @@ class Engine:
                                 torch.empty((S, max_cp), dtype=torch.int64, device=dev),
                                 torch.empty((S, max_cp), dtype=torch.int64, device=dev),
                                 torch.empty((S, max_cp), dtype=torch.float64, device=dev),
-                                torch.empty(S, dtype=torch.int32, device=dev))
+                                torch.empty(S, dtype=torch.int32, device=dev),
+                                torch.empty((S, max_cp), dtype=torch.float64, device=dev))
         rc = self._L.mt4g_ks_segment_host(self._h, ptr, offsets.ctypes.data_as(ctypes.c_void_p),
                                           steps.ctypes.data_as(ctypes.c_void_p), S, float(alpha), int(min_seg),
                                           int(max_cp), mode, int(chunk_samples), _dev_ptr(out.count, "count"),
                                           _dev_ptr(out.idx, "idx"), _dev_ptr(out.dnum, "dnum"),
                                           _dev_ptr(out.dden, "dden"), _dev_ptr(out.p, "p"),
-                                          _dev_ptr(out.fallback, "fallback"), _stream_handle(stream))
+                                          _dev_ptr(out.fallback, "fallback"), _dev_ptr(out.crit, "crit"),
+                                          _stream_handle(stream))
         self._check(rc)
         status = OK
         if sync:
@@ -453,18 +459,35 @@ NOALLOC_MAX_SERIES, NOALLOC_MAX_SAMPLES, NOALLOC_MAX_STEPS = 4096, 1 << 19, 1 <<
 def ks_scan_noalloc(samples, offsets, steps, out, stream=None) -> int:
     """mt4g_ks_scan_noalloc: the top-level scan without any allocation by the library.
 
-    For callers that cannot allocate (memory owned by another pool, an ongoing stream
-    capture, allocation forbidden after start-up).  ``out`` must be a ScanResult of
-    preallocated device tensors; returns the C status code.  Runs on the current device and
-    synchronises ``stream``.  Limits: NOALLOC_MAX_SERIES series, NOALLOC_MAX_SAMPLES samples,
-    NOALLOC_MAX_STEPS steps in total.
+    For callers that cannot allocate device memory: code running inside a memory pool or
+    arena that someone else owns, or a process that forbids allocation after start-up.
+    ``out`` must be a ScanResult of preallocated device tensors (int32, int64, int64,
+    float64, at least S elements each) on the device of ``samples``; returns the C status
+    code.  Runs on the device of ``samples`` and synchronises ``stream``.  Limits:
+    NOALLOC_MAX_SERIES series, NOALLOC_MAX_SAMPLES samples, NOALLOC_MAX_STEPS steps in total.
     """
+    import torch
     L = load_library()
     offsets, steps = _host_tables(offsets, steps)
-    return int(L.mt4g_ks_scan_noalloc(_dev_ptr(samples, "samples"), offsets.ctypes.data_as(ctypes.c_void_p),
-                                      steps.ctypes.data_as(ctypes.c_void_p), steps.shape[0], _dev_ptr(out.k, "k"),
-                                      _dev_ptr(out.dnum, "dnum"), _dev_ptr(out.dden, "dden"), _dev_ptr(out.p, "p"),
-                                      _stream_handle(stream)))
+    S = steps.shape[0]
+    want = (("k", out.k, torch.int32), ("dnum", out.dnum, torch.int64), ("dden", out.dden, torch.int64),
+            ("p", out.p, torch.float64))
+    ptrs = [_dev_ptr(samples, "samples")] + [_dev_ptr(t, name) for name, t, _ in want]
+    if samples.dtype not in (torch.int32, torch.uint32):
+        raise Mt4gError(EINVAL, "samples must hold 32-bit words (int32 or uint32)")
+    if S and samples.numel() < int(offsets[-1]):
+        raise Mt4gError(EINVAL, "samples holds fewer elements than offsets[-1]")
+    for name, t, dt in want:
+        if t.dtype != dt:
+            raise Mt4gError(EINVAL, f"out.{name} must be {dt}")
+        if t.numel() < S:
+            raise Mt4gError(EINVAL, f"out.{name} holds fewer than S elements")
+        if t.device != samples.device:
+            raise Mt4gError(EINVAL, f"out.{name} is not on the device of samples")
+    with torch.cuda.device(samples.device):
+        return int(L.mt4g_ks_scan_noalloc(ptrs[0], offsets.ctypes.data_as(ctypes.c_void_p),
+                                          steps.ctypes.data_as(ctypes.c_void_p), S, *ptrs[1:],
+                                          _stream_handle(stream)))
 
 
 def to_device_samples(samples: np.ndarray, device="cuda"):

@@ -167,6 +167,7 @@ struct Buffers {
     uint8_t *cp_flag;
     int64_t *cp_num, *cp_den;
     double *cp_p;
+    double *cp_crit;
     WorkItem *items;
     int32_t *ready;
     uint32_t *gcount;
@@ -193,6 +194,7 @@ size_t carve(void *base, const Plan &P, Buffers &B, size_t *ready_off) {
     B.cp_num = c.take<int64_t>(P.sumT);
     B.cp_den = c.take<int64_t>(P.sumT);
     B.cp_p = c.take<double>(P.sumT);
+    B.cp_crit = c.take<double>(P.sumT);
     B.red = c.take<double>(P.reduced ? P.sumT : 0);
     B.rank = c.take<uint32_t>(P.reduced ? P.sumT : 0);
     B.gcount = c.take<uint32_t>(P.cap);
@@ -519,6 +521,7 @@ int enqueue_pipeline(mt4g_ctx *ctx, const uint32_t *samples, Plan &P, RunParams 
     R.cp_num = B.cp_num;
     R.cp_den = B.cp_den;
     R.cp_p = B.cp_p;
+    R.cp_crit = B.cp_crit;
     return (int)epoch;  // >= 0
 }
 
@@ -728,7 +731,7 @@ static int scan_body(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offs
 
 static int segment_body(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets, const int32_t *steps,
                         int64_t S, double alpha, int32_t min_seg, int32_t max_cp, int32_t mode, int32_t *cp_count,
-                        int32_t *cp_idx, int64_t *dnum, int64_t *dden, double *p, int32_t *fallback,
+                        int32_t *cp_idx, int64_t *dnum, int64_t *dden, double *p, int32_t *fallback, double *crit,
                         void *cuda_stream) {
     int rc = MT4G_OK;
     if (!(alpha > 0.0 && alpha < 1.0)) return fail(ctx, MT4G_EINVAL, "alpha must be in (0, 1)");
@@ -753,6 +756,9 @@ static int segment_body(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *o
     if (epoch < 0) return epoch;
     R.mode = P.learned ? kRunLearned : kRunSegment;
     R.alpha = alpha;
+    // Eq. 1's constant -1/2 ln(alpha / 2), once on the host; each accepted split multiplies it
+    // by (n_L + n_R) / (n_L n_R) (critical value beside the change point)
+    R.crit_c = -0.5 * log(alpha / 2.0);
     CUDA_TRY(ctx, cudaMemsetAsync(B.cp_flag, 0, (size_t)P.sumT, st));
     if (P.learned) {
         rc = enqueue_proposals(ctx, samples, P, B, R, st);
@@ -765,8 +771,8 @@ static int segment_body(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *o
     if (!P.learned) mark(ctx, 3, st);
     CUDA_TRY(ctx, launch_queue_run(R, R.rk ? ctx->grid_sweep : ctx->grid, (uint32_t)epoch, st));
     mark(ctx, 4, st);
-    CUDA_TRY(ctx, launch_collect(B.desc, P.S, B.cp_flag, B.cp_num, B.cp_den, B.cp_p, max_cp, cp_count, cp_idx, dnum,
-                                 dden, p, B.q, st));
+    CUDA_TRY(ctx, launch_collect(B.desc, P.S, B.cp_flag, B.cp_num, B.cp_den, B.cp_p, B.cp_crit, max_cp, cp_count,
+                                 cp_idx, dnum, dden, p, crit, B.q, st));
     if (fallback)
         CUDA_TRY(ctx, cudaMemcpyAsync(fallback, B.fallback, P.S * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
     return finish_call(ctx, B, st);
@@ -921,27 +927,27 @@ int mt4g_ks_scan(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets,
 
 int mt4g_ks_segment(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets, const int32_t *steps, int64_t S,
                     double alpha, int32_t min_seg, int32_t max_cp, int32_t mode, int32_t *cp_count, int32_t *cp_idx,
-                    int64_t *dnum, int64_t *dden, double *p, int32_t *fallback, void *cuda_stream) {
+                    int64_t *dnum, int64_t *dden, double *p, int32_t *fallback, double *crit, void *cuda_stream) {
     NvtxRange nvtx("mt4g_ks_segment");
     int rc = begin_call(ctx);
     if (rc) return rc;
-    const void *outs[6] = {cp_count, cp_idx, dnum, dden, p, fallback};
+    const void *outs[7] = {cp_count, cp_idx, dnum, dden, p, fallback, crit};
     const uint64_t key = ctx->use_graph ? call_key(ctx, 2, samples, offsets, steps, S, mode, alpha, min_seg, max_cp,
-                                                   outs, 6, cuda_stream)
+                                                   outs, 7, cuda_stream)
                                         : 0;
     return run_maybe_graph(
         ctx, key, graph_pin_need(S), (cudaStream_t)cuda_stream,
         [&] { return presize_for(ctx, offsets, steps, S, mode, min_seg); },
         [&](cudaStream_t s) {
             return segment_body(ctx, samples, offsets, steps, S, alpha, min_seg, max_cp, mode, cp_count, cp_idx, dnum,
-                                dden, p, fallback, (void *)s);
+                                dden, p, fallback, crit, (void *)s);
         });
 }
 
 int mt4g_ks_segment_host(mt4g_ctx *ctx, const uint32_t *samples_host, const int64_t *offsets, const int32_t *steps,
                          int64_t S, double alpha, int32_t min_seg, int32_t max_cp, int32_t mode,
                          int64_t chunk_samples, int32_t *cp_count, int32_t *cp_idx, int64_t *dnum, int64_t *dden,
-                         double *p, int32_t *fallback, void *cuda_stream) {
+                         double *p, int32_t *fallback, double *crit, void *cuda_stream) {
     NvtxRange nvtx("mt4g_ks_segment_host");
     int rc = begin_call(ctx);
     if (rc) return rc;
@@ -1039,7 +1045,8 @@ int mt4g_ks_segment_host(mt4g_ctx *ctx, const uint32_t *samples_host, const int6
         rc = segment_body(ctx, (const uint32_t *)ctx->hin[b], loc.data(), steps + s0, n, alpha, min_seg, max_cp, mode,
                           cp_count + s0, max_cp ? cp_idx + s0 * max_cp : cp_idx, max_cp ? dnum + s0 * max_cp : dnum,
                           max_cp ? dden + s0 * max_cp : dden, max_cp ? p + s0 * max_cp : p,
-                          fallback ? fallback + s0 : nullptr, (void *)st);
+                          fallback ? fallback + s0 : nullptr, (crit && max_cp) ? crit + s0 * max_cp : nullptr,
+                          (void *)st);
         ctx->hdr_dst = nullptr;
         ctx->up_stream = nullptr;
         if (rc) return rc;

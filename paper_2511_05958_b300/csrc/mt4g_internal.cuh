@@ -7,7 +7,7 @@
 //   labA/labB  uint16[Ntot]     step labels travelling with the keys (final in labA)
 //   runs       int32[Ntot + S]  per series: start of each run of equal values,
 //                               runs[run_base + j], j in [0, U_s], last = N_s
-//   cp_flag/num/den/p [sum T]   per step: a change point accepted at that step
+//   cp_flag/num/den/p/crit [sum T]   per step: a change point accepted at that step
 //   queue      WorkItem[cap] + ready[cap] + gcount[cap]   the device work queue
 #pragma once
 #include <cuda_runtime.h>
@@ -142,6 +142,8 @@ struct RunParams {
     int64_t *cp_num;
     int64_t *cp_den;
     double *cp_p;
+    double *cp_crit;  // Eq. 1 critical value of the accepted split
+    double crit_c;    // -1/2 ln(alpha / 2)
     // learned segmentation
     const int32_t *win_center;  // [S * n_win], -1 = none
     int32_t n_win;
@@ -181,10 +183,11 @@ int queue_grid_sweep(int device);  // CTAs of the kernel with the run sweep
 // kStatusCheck in *status on any violation; reads only within each series' own ranges.
 cudaError_t launch_check_sort(const SeriesDesc *desc, int64_t S, const uint16_t *lab, const uint16_t *rk,
                               const int32_t *runs, int32_t *status, cudaStream_t st);
+// crit (optional, may be null): the critical value of each reported change point.
 cudaError_t launch_collect(const SeriesDesc *desc, int64_t S, const uint8_t *cp_flag, const int64_t *cp_num,
-                           const int64_t *cp_den, const double *cp_p, int32_t max_cp, int32_t *cp_count,
-                           int32_t *cp_idx, int64_t *dnum, int64_t *dden, double *p, QueueHeader *q,
-                           cudaStream_t st);
+                           const int64_t *cp_den, const double *cp_p, const double *cp_crit, int32_t max_cp,
+                           int32_t *cp_count, int32_t *cp_idx, int64_t *dnum, int64_t *dden, double *p, double *crit,
+                           QueueHeader *q, cudaStream_t st);
 
 // gate (optional): a device counter; when it reads 0 the proposal kernels return at once (a
 // learned call whose every series the run sweep takes uses no proposal).

@@ -2,12 +2,11 @@
 //
 // Some callers cannot allocate device memory at all: code that runs inside a memory pool
 // or arena owned by someone else (a framework's caching allocator, an embedded runtime
-// with a fixed budget), callers in a CUDA graph that is being captured, or processes whose
-// allocation calls are forbidden after start-up.  For them this entry point runs the same
-// sort and all-splits scan as mt4g_ks_scan, but every scratch buffer is carved from one
-// file-scope device array of kNoAllocBytes, which each GPU that loads the library holds
-// until the process exits.  Host-side tables go through a static host buffer, so the
-// call allocates no host memory either.
+// with a fixed budget), or processes whose allocation calls are forbidden after start-up.
+// For them this entry point runs the same sort and all-splits scan as mt4g_ks_scan, but
+// every scratch buffer is carved from one file-scope device array of kNoAllocBytes, which
+// each GPU that loads the library holds until the process exits.  Host-side tables go
+// through a static host buffer, so the call allocates no host memory either.
 //
 // Limits (checked before any GPU work, MT4G_EINVAL beyond them): at most kNoAllocSeries
 // series, kNoAllocSamples samples and kNoAllocSteps steps in total.
@@ -16,10 +15,11 @@
 // parts that must start at zero (queue flags and counters) are cleared by each call.
 // Calls whose GPU work overlaps (on different streams, or from several host threads)
 // race on the array; host-side staging is serialised by a mutex.  The first call on a
-// device looks up the array's device address (cudaGetSymbolAddress) and caches it, so
-// that first call should come before any stream capture.  The call returns after its
-// results are written (it synchronises the stream) so that it can report device-side
-// status without a context.
+// device looks up the array's device address (cudaGetSymbolAddress) and caches it.  The
+// call returns after its results are written (it synchronises the stream) so that it can
+// report device-side status without a context; when an enqueue fails part way, it still
+// waits for the work already enqueued, so that nothing of a failed call runs on the array
+// after it returns.
 #include <cstring>
 #include <mutex>
 
@@ -149,11 +149,15 @@ extern "C" int mt4g_ks_scan_noalloc(const uint32_t *samples, const int64_t *offs
         sb += d.T;
         nb += seg_chunks(d.T, 1, 1);
     }
-    const size_t bytes_tables = (size_t)((unsigned char *)(hbase + S) - h);
-    (void)bytes_tables;
-#define NA_TRY(expr)                                  \
-    do {                                              \
-        if ((expr) != cudaSuccess) return MT4G_ECUDA; \
+    // After the first enqueue, a failure drains the stream before returning: the next call
+    // must not find this call's copies or kernels still working on the shared array.
+#define NA_TRY(expr)                            \
+    do {                                        \
+        if ((expr) != cudaSuccess) {            \
+            (void)cudaStreamSynchronize(st);    \
+            (void)cudaGetLastError();           \
+            return MT4G_ECUDA;                  \
+        }                                       \
     } while (0)
     NA_TRY(cudaMemcpyAsync(db + L.off_hdr, h, sizeof(QueueHeader), cudaMemcpyHostToDevice, st));
     NA_TRY(cudaMemcpyAsync(db + L.off_desc, hd, S * sizeof(SeriesDesc), cudaMemcpyHostToDevice, st));
@@ -191,7 +195,7 @@ extern "C" int mt4g_ks_scan_noalloc(const uint32_t *samples, const int64_t *offs
     R.dden_out = dden_out;
     R.p_out = p_out;
     const int grid = queue_grid(dev);
-    if (grid <= 0) return MT4G_ECUDA;
+    NA_TRY(grid > 0 ? cudaSuccess : cudaErrorInvalidConfiguration);
     NA_TRY(launch_queue_run(R, grid, epoch, st));
     int32_t status = 0;
     NA_TRY(cudaMemcpyAsync(&status, &q->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));

@@ -571,23 +571,31 @@ __device__ __forceinline__ void warp_best(int &bk, uint64_t &bg, int lo, int hi)
 // adds H to l at its own run (the run index of every sample comes from the sort), so an
 // update costs O(m), and the values at all runs follow from one pass over l.
 //
-// Lane L owns a contiguous block of runs [b0, b1).  Within the block it accumulates the
-// values relative to the run before the block,
-//     v_k(c) - v_k(b0 - 1) = sum_{b0 <= c' <= c} l_k(c') - a (C_c - C_{b0-1}),
+// Lane L owns the block of R consecutive runs [L R, L R + R), R = ceil(U' / 32) rounded up to
+// a multiple of 4, so that every lane walks the same number of runs and needs no per-run
+// bounds test; positions at or past U' hold l = 0 and C = N (= m H), which repeat the value
+// at the last run, v_k(U' - 1) = H m a - a m H = 0.  Within the block the lane accumulates
+// the values relative to the run before the block,
+//     v_k(c) - v_k(L R - 1) = sum_{L R <= c' <= c} l_k(c') - a (C_c - C_{L R - 1}),
 // a sum over the block's samples of H (left) or 0, minus a each, so below m H^2 in magnitude,
 // and keeps their max and min.  The block's own sum of l, scanned across the warp, then
-// gives v_k(b0 - 1) and so the block's true max and min; the warp maximum of the moduli is
+// gives v_k(L R - 1) and so the block's true max and min; the warp maximum of the moduli is
 // g_k.  The sweep takes segments with m H^2 < 2^31, where every quantity above is an exact
 // 32-bit integer.
-struct __align__(16) SweepStage {
-    uint32_t l[kSweepMaxRuns];    // l of compact run c; during setup the count of run r, then C_c
-    uint16_t map[kSweepMaxRuns];  // run -> compact run
-};
+//
+// Layout: the l of lane L's block sits at words [L Rs, L Rs + R) of the stage, Rs = R when
+// R = 4 mod 8 and R + 4 otherwise; a lane reads its block four runs at a time (16-byte
+// loads), and with Rs = 4 mod 8 the eight lanes of a quarter warp start on eight different
+// four-bank groups, so the loads are free of bank conflicts.  Each lane keeps its block's C
+// in registers (they do not change during a segment's sweep).
+constexpr int kSweepMaxR = 48;                       // ceil(kSweepMaxRuns / 32), a multiple of 4
+constexpr int kSweepLWords = 32 * (kSweepMaxR + 4);  // largest padded layout
+static_assert(kSweepMaxRuns <= 32 * kSweepMaxR && kSweepMaxR % 8 == 0, "lane blocks of kSweepMaxR runs");
 
-// Largest lane block: ceil(kSweepMaxRuns / 32) made even and, from 8 on, 2 mod 4.  Each lane
-// keeps its block's C_c in registers (they do not change during a segment's sweep).
-constexpr int kSweepMaxR = 50;
-static_assert(kSweepMaxRuns <= 32 * 48, "lane blocks above kSweepMaxR runs");
+struct __align__(16) SweepStage {
+    uint32_t l[kSweepLWords];     // setup: count of series run r, then C of compact run c; sweep: l by layout position
+    uint16_t map[kSweepMaxRuns];  // series run -> layout position of its compact run
+};
 
 union __align__(16) WarpSmem {
     WarpStage ws;
@@ -604,46 +612,91 @@ __device__ __forceinline__ int eff_kpt(const RunParams &P, const SeriesDesc &d, 
     return d.kpt ? d.kpt : (sweepable(P, d, H) ? 0 : 1);
 }
 
-// l[idx] += w for every active lane.  A shared-memory reduction without return: the warp
+// l[map[r]] += w for every active lane.  A shared-memory reduction without return: the warp
 // does not wait for it, and lanes that hit the same run are serialised by the hardware.
-__device__ __forceinline__ void lc_add(SweepStage &ss, uint32_t idx, uint32_t w, bool act) {
-    if (act) atomicAdd(&ss.l[idx], w);
+__device__ __forceinline__ void lc_add(SweepStage &ss, uint32_t r, uint32_t w, bool act) {
+    if (act) atomicAdd(&ss.l[ss.map[r]], w);
 }
 
-constexpr int kSweepPre = 4;  // run indices of one step held per lane (the first 128 samples)
+// Run indices of one step held per lane between splits.  Vector form (series offset and m
+// multiples of 4, so a step's row is 8-byte aligned): lane L holds samples 4L .. 4L + 3 of
+// the step's first 128 as one 8-byte load.  Scalar form: samples L + 32 q, q < 4.
+template <bool VEC>
+struct StepBuf {
+    uint32_t v[VEC ? 2 : 4];
+};
 
-// Run indices of step t into registers: slot q holds sample lane + 32 q.
+template <bool VEC>
 __device__ __forceinline__ void sweep_load_step(const uint16_t *__restrict__ rk, int64_t t, int m, int lane,
-                                                uint32_t (&buf)[kSweepPre]) {
+                                                StepBuf<VEC> &buf) {
     const uint16_t *src = rk + t * (int64_t)m;
+    if constexpr (VEC) {
+        uint2 x = make_uint2(0u, 0u);
+        if (4 * lane < m) x = __ldg(reinterpret_cast<const uint2 *>(src) + lane);
+        buf.v[0] = x.x;
+        buf.v[1] = x.y;
+    } else {
 #pragma unroll
-    for (int q = 0; q < kSweepPre; q++) {
-        const int j = lane + 32 * q;
-        buf[q] = 0u;
-        if (32 * q < m && j < m) buf[q] = (uint32_t)__ldg(src + j);
+        for (int q = 0; q < 4; q++) {
+            const int j = lane + 32 * q;
+            buf.v[q] = (32 * q < m && j < m) ? (uint32_t)__ldg(src + j) : 0u;
+        }
     }
 }
 
 // Move the samples of step t to the left part: l grows by H at each sample's run.  `buf`
 // holds the step's first 128 run indices (sweep_load_step); the rest are read here.
+template <bool VEC>
 __device__ __forceinline__ void sweep_apply_step(SweepStage &ss, const uint16_t *__restrict__ rk, int64_t t, int m,
-                                                 uint32_t H, int lane, const uint32_t (&buf)[kSweepPre]) {
+                                                 uint32_t H, int lane, const StepBuf<VEC> &buf) {
+    const uint16_t *src = rk + t * (int64_t)m;
+    if constexpr (VEC) {
+        const bool act = 4 * lane < m;
+        lc_add(ss, buf.v[0] & 0xffffu, H, act);
+        lc_add(ss, buf.v[0] >> 16, H, act);
+        lc_add(ss, buf.v[1] & 0xffffu, H, act);
+        lc_add(ss, buf.v[1] >> 16, H, act);
+        for (int j0 = 128; j0 < m; j0 += 128) {
+            const bool a2 = j0 + 4 * lane < m;
+            uint2 x = make_uint2(0u, 0u);
+            if (a2) x = __ldg(reinterpret_cast<const uint2 *>(src + j0) + lane);
+            lc_add(ss, x.x & 0xffffu, H, a2);
+            lc_add(ss, x.x >> 16, H, a2);
+            lc_add(ss, x.y & 0xffffu, H, a2);
+            lc_add(ss, x.y >> 16, H, a2);
+        }
+    } else {
 #pragma unroll
-    for (int q = 0; q < kSweepPre; q++) {
-        if (32 * q < m) {
-            const bool act = lane + 32 * q < m;
-            lc_add(ss, act ? (uint32_t)ss.map[buf[q]] : 0u, H, act);
+        for (int q = 0; q < 4; q++)
+            if (32 * q < m) lc_add(ss, buf.v[q], H, lane + 32 * q < m);
+        for (int j0 = 128; j0 < m; j0 += 32) {
+            const bool act = j0 + lane < m;
+            lc_add(ss, act ? (uint32_t)__ldg(src + j0 + lane) : 0u, H, act);
         }
     }
-    const uint16_t *src = rk + t * (int64_t)m;
-    for (int j0 = 32 * kSweepPre; j0 < m; j0 += 32) {
-        const bool act = j0 + lane < m;
-        lc_add(ss, act ? (uint32_t)ss.map[__ldg(src + j0 + lane)] : 0u, H, act);
-    }
+}
+
+// Four runs of a lane's block: running l sum hc, values hc - a C relative to the run before
+// the block, their max and min (three-input integer max / min).
+__device__ __forceinline__ void sweep_eval4(const uint4 q, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                            uint32_t na, uint32_t &hc, int32_t &mx, int32_t &mn) {
+    hc += q.x;
+    const int32_t v0 = (int32_t)(hc + na * c0);
+    hc += q.y;
+    const int32_t v1 = (int32_t)(hc + na * c1);
+    mx = __vimax3_s32(mx, v0, v1);
+    mn = __vimin3_s32(mn, v0, v1);
+    hc += q.z;
+    const int32_t v2 = (int32_t)(hc + na * c2);
+    hc += q.w;
+    const int32_t v3 = (int32_t)(hc + na * c3);
+    mx = __vimax3_s32(mx, v2, v3);
+    mn = __vimin3_s32(mn, v2, v3);
 }
 
 // Best split (k, g) over A <= k <= B of segment [lo, hi) of a run-sweep series; every lane
 // gets it.  `nonempty` = U', the runs with in-segment samples.
+template <bool VEC>
 __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int hi, int A, int B, SweepStage &ss,
                            int &bk, uint64_t &bg, int &nonempty) {
     const int lane = threadIdx.x & 31;
@@ -652,7 +705,9 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
     const uint32_t H = (uint32_t)(hi - lo);
     const unsigned lt = lanemask_lt();
 
-    // in-segment samples per run, into l[r]
+    // in-segment samples per series run, into l[r]; during setup map[r] = r, so lc_add counts
+    // at the run itself
+    for (int r = lane; r < U; r += 32) ss.map[r] = (uint16_t)r;
     if (lo == 0 && hi == d.T) {
         const int32_t *rt = P.runs + d.run_base;
         for (int r = lane; r < U; r += 32) ss.l[r] = (uint32_t)(__ldg(rt + r + 1) - __ldg(rt + r));
@@ -660,20 +715,41 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
         for (int r = lane; r < U; r += 32) ss.l[r] = 0;
         __syncwarp();
         const int64_t e1 = (int64_t)hi * m;
-        for (int64_t e0 = (int64_t)lo * m; e0 < e1; e0 += 512) {  // 16 loads in flight per lane
-            uint32_t r16[16];
+        if constexpr (VEC) {  // rows are 8-byte aligned: four run indices per load, 1024 per round
+            const uint2 *src = reinterpret_cast<const uint2 *>(rk);
+            for (int64_t e0 = (int64_t)lo * m; e0 < e1; e0 += 1024) {
+                uint2 x8[8];
 #pragma unroll
-            for (int q = 0; q < 16; q++) {
-                const int64_t e = e0 + 32 * q + lane;
-                r16[q] = e < e1 ? (uint32_t)__ldg(rk + e) : 0u;
+                for (int q = 0; q < 8; q++) {
+                    const int64_t e = e0 + 128 * q + 4 * lane;
+                    x8[q] = e < e1 ? __ldg(src + (e >> 2)) : make_uint2(0u, 0u);
+                }
+#pragma unroll
+                for (int q = 0; q < 8; q++) {
+                    const bool act = e0 + 128 * q + 4 * lane < e1;
+                    lc_add(ss, x8[q].x & 0xffffu, 1u, act);
+                    lc_add(ss, x8[q].x >> 16, 1u, act);
+                    lc_add(ss, x8[q].y & 0xffffu, 1u, act);
+                    lc_add(ss, x8[q].y >> 16, 1u, act);
+                }
             }
+        } else {
+            for (int64_t e0 = (int64_t)lo * m; e0 < e1; e0 += 512) {  // 16 loads in flight per lane
+                uint32_t r16[16];
 #pragma unroll
-            for (int q = 0; q < 16; q++) lc_add(ss, r16[q], 1u, e0 + 32 * q + lane < e1);
+                for (int q = 0; q < 16; q++) {
+                    const int64_t e = e0 + 32 * q + lane;
+                    r16[q] = e < e1 ? (uint32_t)__ldg(rk + e) : 0u;
+                }
+#pragma unroll
+                for (int q = 0; q < 16; q++) lc_add(ss, r16[q], 1u, e0 + 32 * q + lane < e1);
+            }
         }
     }
     __syncwarp();
     // compaction, 32 runs per round: a run's compact slot is never above its own index, and
-    // every round reads its counts before it writes, so the later rounds' counts survive
+    // every round reads its counts before it writes, so the later rounds' counts survive.
+    // Absent runs keep a stale map entry; no sample of the segment refers to them.
     uint32_t nc = 0, cs = 0;  // runs kept so far, in-segment samples so far
     for (int r0 = 0; r0 < U; r0 += 32) {
         const int r = r0 + lane;
@@ -696,92 +772,71 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
         __syncwarp();
     }
     const int Uc = (int)nc;
+    const uint32_t N = cs;  // m H
     nonempty = Uc;
-    // an odd count is padded with a copy of the last run (l = 0, same C): it repeats the
-    // last value and changes no maximum, and lets every block read whole pairs
-    const int Ue = Uc + (Uc & 1);
-    if ((Uc & 1) && lane == 0) ss.l[Uc] = cs;
-    // blocks: R runs per lane, R even; R = 2 mod 4 for larger R keeps the 16-byte pair loads of
-    // a quarter warp on distinct banks
-    int R = (Ue + 31) / 32;
-    R += R & 1;
-    if (R >= 8 && (R & 3) == 0) R += 2;
-    const int b0 = min(lane * R, Ue), b1 = min(b0 + R, Ue);
-    const int npair = (b1 - b0) >> 1;
-    const uint2 *pairs = reinterpret_cast<const uint2 *>(&ss.l[b0]);
-    __syncwarp();
-    const uint32_t Cb = b0 > 0 ? ss.l[b0 - 1] : 0u;  // in-segment samples below the block
-    // C of the block's runs; past the block's end the last run's C, so that a pair evaluated
-    // there with l = 0 repeats the last value and changes neither max nor min
-    const uint32_t Clast = b1 > b0 ? ss.l[b1 - 1] : 0u;
+    int R = (Uc + 31) >> 5;
+    R = max(4, (R + 3) & ~3);
+    const int Rs = (R & 7) ? R : R + 4;
+    const int nq = R >> 2;  // quads per block
+    const int b0 = lane * R;
+    const uint32_t Cb = b0 == 0 ? 0u : (b0 <= Uc ? ss.l[b0 - 1] : N);  // in-segment samples below the block
     uint32_t Cr[kSweepMaxR];
 #pragma unroll
-    for (int j = 0; j < kSweepMaxR; j++) Cr[j] = b0 + j < b1 ? ss.l[b0 + j] : Clast;
+    for (int j = 0; j < kSweepMaxR; j++) Cr[j] = (j < R && b0 + j < Uc) ? ss.l[b0 + j] : N;
     __syncwarp();
-    for (int c = lane; c < Ue; c += 32) ss.l[c] = 0u;
+    // compact index -> layout position, then l = 0 over the whole layout
+    for (int r = lane; r < U; r += 32) {
+        const uint32_t ci = ss.map[r];
+        ss.map[r] = (uint16_t)((ci / (uint32_t)R) * (uint32_t)Rs + ci % (uint32_t)R);
+    }
+    for (int w = lane; w < 32 * Rs; w += 32) ss.l[w] = 0u;
     __syncwarp();
 
     for (int t = lo; t < A; t++) {
-        uint32_t buf[kSweepPre];
-        sweep_load_step(rk, t, m, lane, buf);
-        sweep_apply_step(ss, rk, t, m, H, lane, buf);
+        StepBuf<VEC> buf;
+        sweep_load_step<VEC>(rk, t, m, lane, buf);
+        sweep_apply_step<VEC>(ss, rk, t, m, H, lane, buf);
     }
-    uint32_t nxt[kSweepPre];
-    sweep_load_step(rk, A, m, lane, nxt);
+    const uint4 *lq = reinterpret_cast<const uint4 *>(&ss.l[lane * Rs]);
+    StepBuf<VEC> nxt;
+    sweep_load_step<VEC>(rk, A, m, lane, nxt);
     bk = kNoK;
     bg = 0;
     uint32_t gk = 0;  // g of split kb + lane
     int kb = A;
     for (int k = A; k <= B; k++) {
-        uint32_t cur[kSweepPre];
-#pragma unroll
-        for (int q = 0; q < kSweepPre; q++) cur[q] = nxt[q];
-        if (k + 1 <= B) sweep_load_step(rk, k + 1, m, lane, nxt);  // in flight during this split
+        const StepBuf<VEC> cur = nxt;
+        if (k + 1 <= B) sweep_load_step<VEC>(rk, k + 1, m, lane, nxt);  // in flight during this split
         __syncwarp();
         const uint32_t a = (uint32_t)(k - lo), na = 0u - a;
         const uint32_t h0 = a * Cb;
         uint32_t hc = h0;
         int32_t mx = INT_MIN, mn = INT_MAX;
-        // groups of 4 pairs, loads first; pairs past the block read as l = 0 (see Cr)
+        // the block in groups of two quads (8 runs); nq is the same for every lane
 #pragma unroll
-        for (int g = 0; g < (kSweepMaxR / 2 + 3) / 4; g++) {
-            if (4 * g >= npair) break;
-            uint2 q[4];
-#pragma unroll
-            for (int t = 0; t < 4; t++) {
-                const int j = 4 * g + t;
-                q[t] = (j < kSweepMaxR / 2 && j < npair) ? pairs[j] : make_uint2(0u, 0u);
-            }
-#pragma unroll
-            for (int t = 0; t < 4; t++) {
-                const int j = 4 * g + t;
-                if (j < kSweepMaxR / 2) {
-                    hc += q[t].x;
-                    const int32_t v0 = (int32_t)(hc + na * Cr[2 * j]);
-                    hc += q[t].y;
-                    const int32_t v1 = (int32_t)(hc + na * Cr[2 * j + 1]);
-                    mx = __vimax3_s32(mx, v0, v1);
-                    mn = __vimin3_s32(mn, v0, v1);
-                }
-            }
+        for (int g = 0; g < kSweepMaxR / 8; g++) {
+            if (2 * g >= nq) break;
+            const bool two = 2 * g + 1 < nq;
+            const uint4 q0 = lq[2 * g];
+            uint4 q1 = make_uint4(0u, 0u, 0u, 0u);
+            if (two) q1 = lq[2 * g + 1];
+            sweep_eval4(q0, Cr[8 * g], Cr[8 * g + 1], Cr[8 * g + 2], Cr[8 * g + 3], na, hc, mx, mn);
+            if (two) sweep_eval4(q1, Cr[8 * g + 4], Cr[8 * g + 5], Cr[8 * g + 6], Cr[8 * g + 7], na, hc, mx, mn);
         }
         const uint32_t blk = hc - h0;  // sum of l over the block
         // every lane has read l for split k: step k's samples move left now (reductions the warp
         // does not wait for), and the warp's results for split k follow in registers
         __syncwarp();
-        if (k < B) sweep_apply_step(ss, rk, k, m, H, lane, cur);
+        if (k < B) sweep_apply_step<VEC>(ss, rk, k, m, H, lane, cur);
         uint32_t incl = blk;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(kFull, incl, o);
             if (lane >= o) incl += y;
         }
-        const uint32_t vs = (incl - blk) - a * Cb;  // v_k at the run before the block
-        uint32_t gl = 0;
-        if (npair > 0) {
-            const int32_t bmax = (int32_t)(vs + (uint32_t)mx), bmin = (int32_t)(vs + (uint32_t)mn);
-            gl = max((uint32_t)max(bmax, 0), (uint32_t)max(-bmin, 0));
-        }
+        const uint32_t vs = (incl - blk) - h0;  // v_k at the run before the block
+        const int32_t bmax = (int32_t)(vs + (uint32_t)mx), bmin = (int32_t)(vs + (uint32_t)mn);
+        const uint32_t gl = max((uint32_t)max(bmax, 0), (uint32_t)max(-bmin, 0));
         const uint32_t g = __reduce_max_sync(kFull, gl);
         if (lane == k - kb) gk = g;
         if (k - kb == 31 || k == B) {
@@ -909,6 +964,10 @@ __device__ __noinline__ void finish_segment(const RunParams &P, const SeriesDesc
             P.cp_num[slot] = num;
             P.cp_den[slot] = den;
             P.cp_p[slot] = p;
+            // Eq. 1: d_alpha = sqrt(-1/2 ln(alpha / 2) (n_L + n_R) / (n_L n_R)), products in this
+            // order, each rounded once
+            P.cp_crit[slot] = __dsqrt_rn(__ddiv_rn(__dmul_rn(P.crit_c, (double)N),
+                                                   __dmul_rn((double)(m * a), (double)(m * b))));
             P.cp_flag[slot] = 1;
             accept = 1;
         }
@@ -1115,7 +1174,11 @@ __global__ void __launch_bounds__(SWEEP ? kSweepThreads : kScanThreads, SWEEP ? 
             warp_best(bk, bg, lo, hi);
         } else if (SWEEP && kind == kPlain && eff_kpt(P, d, hi - lo) == 0) {
             if constexpr (SWEEP) {
-                sweep_best(P, d, lo, hi, A, B, *reinterpret_cast<SweepStage *>(&s_stage[warp]), bk, bg, nonempty);
+                SweepStage &ss = *reinterpret_cast<SweepStage *>(&s_stage[warp]);
+                if ((d.off & 3) == 0 && (d.m & 3) == 0)
+                    sweep_best<true>(P, d, lo, hi, A, B, ss, bk, bg, nonempty);
+                else
+                    sweep_best<false>(P, d, lo, hi, A, B, ss, bk, bg, nonempty);
                 my_evals += (unsigned long long)(B - A + 1) * (unsigned long long)nonempty;
                 my_swept++;
             }
@@ -1241,8 +1304,9 @@ __global__ void init_learned_kernel(RunParams P, const float *__restrict__ conf,
 // One warp per series: gather the flagged steps in ascending order.
 __global__ void collect_kernel(const SeriesDesc *__restrict__ desc, int64_t S, const uint8_t *__restrict__ cp_flag,
                                const int64_t *__restrict__ cp_num, const int64_t *__restrict__ cp_den,
-                               const double *__restrict__ cp_p, int32_t max_cp, int32_t *cp_count, int32_t *cp_idx,
-                               int64_t *dnum, int64_t *dden, double *p, QueueHeader *q) {
+                               const double *__restrict__ cp_p, const double *__restrict__ cp_crit, int32_t max_cp,
+                               int32_t *cp_count, int32_t *cp_idx, int64_t *dnum, int64_t *dden, double *p,
+                               double *crit, QueueHeader *q) {
     const int64_t s = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (s >= S) return;
@@ -1260,6 +1324,7 @@ __global__ void collect_kernel(const SeriesDesc *__restrict__ desc, int64_t S, c
                 dnum[o] = cp_num[d.step_base + t];
                 dden[o] = cp_den[d.step_base + t];
                 p[o] = cp_p[d.step_base + t];
+                if (crit) crit[o] = cp_crit[d.step_base + t];
             }
         }
         count += __popc(b);
@@ -1270,6 +1335,7 @@ __global__ void collect_kernel(const SeriesDesc *__restrict__ desc, int64_t S, c
         dnum[o] = 0;
         dden[o] = 0;
         p[o] = 1.0;
+        if (crit) crit[o] = 0.0;
     }
     if (lane == 0) {
         cp_count[s] = count;
@@ -1332,14 +1398,14 @@ cudaError_t launch_init_items(const SeriesDesc *desc, const int32_t *qorder, con
 }
 
 cudaError_t launch_collect(const SeriesDesc *desc, int64_t S, const uint8_t *cp_flag, const int64_t *cp_num,
-                           const int64_t *cp_den, const double *cp_p, int32_t max_cp, int32_t *cp_count,
-                           int32_t *cp_idx, int64_t *dnum, int64_t *dden, double *p, QueueHeader *q,
-                           cudaStream_t st) {
+                           const int64_t *cp_den, const double *cp_p, const double *cp_crit, int32_t max_cp,
+                           int32_t *cp_count, int32_t *cp_idx, int64_t *dnum, int64_t *dden, double *p, double *crit,
+                           QueueHeader *q, cudaStream_t st) {
     if (S <= 0) return cudaSuccess;
     const int warps = 8;
     const unsigned blocks = (unsigned)((S + warps - 1) / warps);
-    collect_kernel<<<blocks, warps * 32, 0, st>>>(desc, S, cp_flag, cp_num, cp_den, cp_p, max_cp, cp_count, cp_idx,
-                                                  dnum, dden, p, q);
+    collect_kernel<<<blocks, warps * 32, 0, st>>>(desc, S, cp_flag, cp_num, cp_den, cp_p, cp_crit, max_cp, cp_count,
+                                                  cp_idx, dnum, dden, p, crit, q);
     return cudaGetLastError();
 }
 

@@ -230,39 +230,122 @@ __device__ void lsd_passes(SortSmem &sm, int passes, const uint32_t *__restrict_
 
 // Values per series the counting path can index: the sort's shared memory as 32-bit counters.
 constexpr uint32_t kFastSpan = (uint32_t)(sizeof(SortSmem) / sizeof(uint32_t));
+// The counting table's base is guessed from the series' first sample, this far below it (a
+// latency series usually starts at its smallest latencies); a value outside the table sends the
+// series to a recount from its true minimum.
+constexpr uint32_t kBaseBelow = 1024;
+constexpr int kCountVec = 4;  // 16-byte loads in flight per thread
 
-// Counting path for a run-sweep series whose values span at most kFastSpan (all threads call
-// it; returns false, with nothing written, when the series has more than kSweepMaxRuns
-// distinct values).  Counts every value in a table indexed by value - vmin, scans the table
-// for the run table (starts of the distinct values in value order) and the order statistics,
-// turns it into a value -> run index table, and writes each sample's run index in input
-// order.  The sorted labels are not produced (kDescNoLabels).
-__device__ bool count_runs(SortSmem &sm, const uint32_t *__restrict__ in, int32_t N, uint32_t vmin, uint32_t vmax,
-                           int32_t *__restrict__ rt, SeriesDesc *__restrict__ ds, uint16_t *__restrict__ rko,
-                           unsigned long long *sweep_stats) {
-    __shared__ uint32_t s_scan[2][kSortWarps];
+// A series' samples as a head of single samples up to the first 16-byte boundary, 16-byte
+// chunks, and a tail of single samples.
+struct VecSplit {
+    int head, nvec;
+};
+__device__ __forceinline__ VecSplit vec_split(const uint32_t *in, int32_t N) {
+    const int head = min(N, (int)(((16u - (uint32_t)((uintptr_t)in & 15u)) & 15u) >> 2));
+    return VecSplit{head, (N - head) >> 2};
+}
+
+// Block-wide min and max (all threads call it; every thread gets the result).  Uses its own
+// shared words, so the counting table, which spans all of SortSmem, stays intact.
+__device__ __forceinline__ void block_minmax(uint32_t &vmin, uint32_t &vmax) {
+    __shared__ uint32_t s_mm[2][kSortWarps + 1];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    uint32_t *cnt = reinterpret_cast<uint32_t *>(&sm);
-    const uint32_t span = vmax - vmin + 1;
-    for (uint32_t i = tid; i < span; i += kSortThreads) cnt[i] = 0;
+    vmax = __reduce_max_sync(kFull, vmax);
+    vmin = __reduce_min_sync(kFull, vmin);
+    __syncthreads();  // the previous call's results may still be read
+    if (lane == 0) {
+        s_mm[0][warp] = vmax;
+        s_mm[1][warp] = vmin;
+    }
     __syncthreads();
-    for (int b0 = 0; b0 < N; b0 += kSortThreads * kSortItems) {
-        uint32_t v[kSortItems];
-#pragma unroll
-        for (int it = 0; it < kSortItems; it++) {
-            const int i = b0 + it * kSortThreads + tid;
-            v[it] = i < N ? __ldg(in + i) - vmin : 0u;
-        }
-#pragma unroll
-        for (int it = 0; it < kSortItems; it++) {
-            const int i = b0 + it * kSortThreads + tid;
-            hist_add(cnt, v[it], __ballot_sync(kFull, i < N));
+    if (warp == 0) {
+        uint32_t v = lane < kSortWarps ? s_mm[0][lane] : 0u;
+        uint32_t u = lane < kSortWarps ? s_mm[1][lane] : 0xffffffffu;
+        v = __reduce_max_sync(kFull, v);
+        u = __reduce_min_sync(kFull, u);
+        if (lane == 0) {
+            s_mm[0][kSortWarps] = v;
+            s_mm[1][kSortWarps] = u;
         }
     }
     __syncthreads();
+    vmax = s_mm[0][kSortWarps];
+    vmin = s_mm[1][kSortWarps];
+}
+
+// One value into the counting table (every lane calls it; lanes with valid = false add nothing).
+// A value outside [base, base + kFastSpan) is not counted and sets `out`.
+__device__ __forceinline__ void count_one(uint32_t *cnt, uint32_t v, uint32_t base, bool valid, bool &out,
+                                          uint32_t &vmin, uint32_t &vmax) {
+    const uint32_t dv = v - base;
+    const bool in_range = dv < kFastSpan;
+    out |= valid && !in_range;
+    if (valid) {
+        vmin = min(vmin, v);
+        vmax = max(vmax, v);
+    }
+    hist_add(cnt, in_range ? dv : 0u, __ballot_sync(kFull, valid && in_range));
+}
+
+// Count every sample's value - base into the table (the sort's shared memory as kFastSpan
+// counters), reading the series once with 16-byte loads; also the series' min and max.  Returns
+// false (the same in every thread) when some value fell outside the table.
+__device__ bool count_values(SortSmem &sm, const uint32_t *__restrict__ in, int32_t N, uint32_t base,
+                             uint32_t &vmin, uint32_t &vmax) {
+    const int tid = threadIdx.x;
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(&sm);
+    for (uint32_t i = tid; i < kFastSpan; i += kSortThreads) cnt[i] = 0;
+    __syncthreads();
+    const VecSplit vs = vec_split(in, N);
+    vmin = 0xffffffffu;
+    vmax = 0;
+    bool out = false;
+    {  // head and tail samples, one per thread of the first warp
+        const int nt = N - vs.head - 4 * vs.nvec;
+        if (tid < 32) {
+            const int i = tid < vs.head ? tid : (tid - vs.head < nt ? vs.head + 4 * vs.nvec + (tid - vs.head) : -1);
+            count_one(cnt, i >= 0 ? __ldg(in + i) : 0u, base, i >= 0, out, vmin, vmax);
+        }
+    }
+    const uint4 *v4 = reinterpret_cast<const uint4 *>(in + vs.head);
+    for (int b0 = 0; b0 < vs.nvec; b0 += kSortThreads * kCountVec) {
+        uint4 x[kCountVec];
+#pragma unroll
+        for (int it = 0; it < kCountVec; it++) {
+            const int i = b0 + it * kSortThreads + tid;
+            x[it] = i < vs.nvec ? __ldg(v4 + i) : make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int it = 0; it < kCountVec; it++) {
+            const bool valid = b0 + it * kSortThreads + tid < vs.nvec;
+            count_one(cnt, x[it].x, base, valid, out, vmin, vmax);
+            count_one(cnt, x[it].y, base, valid, out, vmin, vmax);
+            count_one(cnt, x[it].z, base, valid, out, vmin, vmax);
+            count_one(cnt, x[it].w, base, valid, out, vmin, vmax);
+        }
+    }
+    out = __syncthreads_or(out);
+    block_minmax(vmin, vmax);
+    return !out;
+}
+
+// Counting path, after count_values succeeded: scans the table over [vmin, vmax] for the run
+// table (starts of the distinct values in value order) and the order statistics, turns it into a
+// value -> run index table, and writes each sample's run index in input order (16-byte reads,
+// 8-byte writes where aligned).  All threads call it; returns false, with nothing written, when
+// the series has more than kSweepMaxRuns distinct values.  The sorted labels are not produced
+// (kDescNoLabels).
+__device__ bool count_runs(SortSmem &sm, const uint32_t *__restrict__ in, int32_t N, uint32_t base, uint32_t vmin,
+                           uint32_t vmax, int32_t *__restrict__ rt, SeriesDesc *__restrict__ ds,
+                           uint16_t *__restrict__ rko, unsigned long long *sweep_stats) {
+    __shared__ uint32_t s_scan[2][kSortWarps];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(&sm);
+    const uint32_t t0 = vmin - base, span = vmax - vmin + 1;
     // each thread scans a contiguous piece of the table: distinct values and samples in it
     const uint32_t per = (span + kSortThreads - 1) / kSortThreads;
-    const uint32_t c0 = min(span, (uint32_t)tid * per), c1 = min(span, c0 + per);
+    const uint32_t c0 = t0 + min(span, (uint32_t)tid * per), c1 = t0 + min(span, (uint32_t)tid * per + per);
     uint32_t nd = 0, ns = 0;
     for (uint32_t i = c0; i < c1; i++) {
         const uint32_t c = cnt[i];
@@ -302,9 +385,9 @@ __device__ bool count_runs(SortSmem &sm, const uint32_t *__restrict__ in, int32_
         const uint32_t c = cnt[i];
         if (c == 0u) continue;
         rt[r] = (int32_t)pos;
-        if (qmed - pos < c) ds->median = vmin + i;
-        if (q50 - pos < c) ds->p50 = vmin + i;
-        if (q95 - pos < c) ds->p95 = vmin + i;
+        if (qmed - pos < c) ds->median = base + i;
+        if (q50 - pos < c) ds->p50 = base + i;
+        if (q95 - pos < c) ds->p95 = base + i;
         cnt[i] = r;
         r++;
         pos += c;
@@ -317,20 +400,85 @@ __device__ bool count_runs(SortSmem &sm, const uint32_t *__restrict__ in, int32_
         atomicAdd(sweep_stats + 1, (unsigned long long)N);
     }
     __syncthreads();
-    for (int b0 = 0; b0 < N; b0 += kSortThreads * kSortItems) {
-        uint32_t v[kSortItems];
+    const VecSplit vs = vec_split(in, N);
+    if (tid < 32) {  // head and tail samples
+        const int nt = N - vs.head - 4 * vs.nvec;
+        const int i = tid < vs.head ? tid : (tid - vs.head < nt ? vs.head + 4 * vs.nvec + (tid - vs.head) : -1);
+        if (i >= 0) rko[i] = (uint16_t)cnt[__ldg(in + i) - base];
+    }
+    const uint4 *v4 = reinterpret_cast<const uint4 *>(in + vs.head);
+    uint16_t *o = rko + vs.head;
+    const bool st8 = ((uintptr_t)o & 7u) == 0;  // the same for every thread
+    for (int b0 = 0; b0 < vs.nvec; b0 += kSortThreads * kCountVec) {
+        uint4 x[kCountVec];
 #pragma unroll
-        for (int it = 0; it < kSortItems; it++) {
+        for (int it = 0; it < kCountVec; it++) {
             const int i = b0 + it * kSortThreads + tid;
-            v[it] = i < N ? __ldg(in + i) - vmin : 0u;
+            x[it] = i < vs.nvec ? __ldg(v4 + i) : make_uint4(base, base, base, base);
         }
 #pragma unroll
-        for (int it = 0; it < kSortItems; it++) {
+        for (int it = 0; it < kCountVec; it++) {
             const int i = b0 + it * kSortThreads + tid;
-            if (i < N) rko[i] = (uint16_t)cnt[v[it]];
+            if (i < vs.nvec) {
+                const uint32_t r0 = cnt[x[it].x - base], r1 = cnt[x[it].y - base];
+                const uint32_t r2 = cnt[x[it].z - base], r3 = cnt[x[it].w - base];
+                if (st8) {
+                    reinterpret_cast<uint2 *>(o)[i] = make_uint2(r0 | (r1 << 16), r2 | (r3 << 16));
+                } else {
+                    o[4 * i] = (uint16_t)r0;
+                    o[4 * i + 1] = (uint16_t)r1;
+                    o[4 * i + 2] = (uint16_t)r2;
+                    o[4 * i + 3] = (uint16_t)r3;
+                }
+            }
         }
     }
     return true;
+}
+
+// Pass-0 digit counts and the min and max of the series in one read (16-byte loads).
+__device__ void digit0_minmax(SortSmem &sm, const uint32_t *__restrict__ in, int32_t N, uint32_t &vmin,
+                              uint32_t &vmax) {
+    const int tid = threadIdx.x;
+    if (tid < 256) sm.hist[tid] = 0;
+    __syncthreads();
+    vmin = 0xffffffffu;
+    vmax = 0;
+    const VecSplit vs = vec_split(in, N);
+    if (tid < 32) {
+        const int nt = N - vs.head - 4 * vs.nvec;
+        const int i = tid < vs.head ? tid : (tid - vs.head < nt ? vs.head + 4 * vs.nvec + (tid - vs.head) : -1);
+        const uint32_t v = i >= 0 ? __ldg(in + i) : 0u;
+        if (i >= 0) {
+            vmin = min(vmin, v);
+            vmax = max(vmax, v);
+        }
+        hist_add(sm.hist, v & 255u, __ballot_sync(kFull, i >= 0));
+    }
+    const uint4 *v4 = reinterpret_cast<const uint4 *>(in + vs.head);
+    for (int b0 = 0; b0 < vs.nvec; b0 += kSortThreads * kCountVec) {
+        uint4 x[kCountVec];
+#pragma unroll
+        for (int it = 0; it < kCountVec; it++) {
+            const int i = b0 + it * kSortThreads + tid;
+            x[it] = i < vs.nvec ? __ldg(v4 + i) : make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int it = 0; it < kCountVec; it++) {
+            const bool valid = b0 + it * kSortThreads + tid < vs.nvec;
+            const unsigned vm = __ballot_sync(kFull, valid);
+            if (valid) {
+                vmin = min(min(vmin, x[it].x), min(x[it].y, min(x[it].z, x[it].w)));
+                vmax = max(max(vmax, x[it].x), max(x[it].y, max(x[it].z, x[it].w)));
+            }
+            hist_add(sm.hist, x[it].x & 255u, vm);
+            hist_add(sm.hist, x[it].y & 255u, vm);
+            hist_add(sm.hist, x[it].z & 255u, vm);
+            hist_add(sm.hist, x[it].w & 255u, vm);
+        }
+    }
+    __syncthreads();
+    block_minmax(vmin, vmax);
 }
 
 __global__ void __launch_bounds__(kSortThreads, 2)
@@ -346,76 +494,27 @@ sort_series_kernel(const uint32_t *__restrict__ samples, SeriesDesc *__restrict_
     const int32_t m = d.m;
     const int32_t N = d.T * m;
     const uint32_t *in = samples + off;
-
-    // ---- largest value and the digit counts of pass 0, in one read
-    if (tid < 256) sm.hist[tid] = 0;
-    __syncthreads();
-    uint32_t vmax = 0, vmin = 0xffffffffu;
-    for (int b0 = 0; b0 < N; b0 += kSortThreads * kSortItems) {
-        // all loads of the round first, so they are in flight together
-        uint32_t v[kSortItems];
-#pragma unroll
-        for (int it = 0; it < kSortItems; it++) {
-            const int i = b0 + it * kSortThreads + tid;
-            v[it] = i < N ? __ldg(in + i) : 0u;
-        }
-#pragma unroll
-        for (int it = 0; it < kSortItems; it++) {
-            const int i = b0 + it * kSortThreads + tid;
-            const unsigned vm = __ballot_sync(kFull, i < N);
-            vmax = max(vmax, v[it]);
-            if (i < N) vmin = min(vmin, v[it]);
-            hist_add(sm.hist, v[it] & 255u, vm);
-        }
-    }
-    vmax = __reduce_max_sync(kFull, vmax);
-    vmin = __reduce_min_sync(kFull, vmin);
-    if (lane == 0) {
-        sm.tmp[warp] = vmax;
-        sm.tmp[kSortWarps + warp] = vmin;
-    }
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t v = lane < kSortWarps ? sm.tmp[lane] : 0u;
-        uint32_t u = lane < kSortWarps ? sm.tmp[kSortWarps + lane] : 0xffffffffu;
-        v = __reduce_max_sync(kFull, v);
-        u = __reduce_min_sync(kFull, u);
-        __syncwarp();
-        if (lane == 0) {
-            sm.tmp[31] = v;
-            sm.tmp[30] = u;
-        }
-    }
-    __syncthreads();
-    vmax = sm.tmp[31];
-    vmin = sm.tmp[30];
-    __syncthreads();
     int32_t *rt = runs + d.run_base;
+    uint32_t vmin, vmax;
 
     // ---- counting path: a run-sweep series with a narrow value span whose every segment the
-    // sweep takes (m T^2 < 2^31) needs only the run table and the run indices
-    if (sweep_stats && d.kpt == 0 && vmax - vmin < kFastSpan &&
-        (uint64_t)m * (uint64_t)d.T * (uint64_t)d.T < (1ull << 31)) {
-        if (count_runs(sm, in, N, vmin, vmax, rt, desc + s, labB + off, sweep_stats)) return;
-        // too many distinct values for the sweep: sort as usual, recounting pass 0's digits
-        __syncthreads();
-        if (tid < 256) sm.hist[tid] = 0;
-        __syncthreads();
-        for (int b0 = 0; b0 < N; b0 += kSortThreads * kSortItems) {
-            uint32_t v[kSortItems];
-#pragma unroll
-            for (int it = 0; it < kSortItems; it++) {
-                const int i = b0 + it * kSortThreads + tid;
-                v[it] = i < N ? __ldg(in + i) : 0u;
-            }
-#pragma unroll
-            for (int it = 0; it < kSortItems; it++) {
-                const int i = b0 + it * kSortThreads + tid;
-                hist_add(sm.hist, v[it] & 255u, __ballot_sync(kFull, i < N));
-            }
+    // sweep takes (m T^2 < 2^31) needs only the run table and the run indices.  One read counts
+    // the values in a table based just below the first sample; if a value falls outside it and
+    // the span still fits, a second read recounts from the minimum.
+    if (sweep_stats && d.kpt == 0 && (uint64_t)m * (uint64_t)d.T * (uint64_t)d.T < (1ull << 31)) {
+        const uint32_t v0 = __ldg(in);
+        // the table [base, base + kFastSpan) must not wrap past 2^32 - 1
+        uint32_t base = min(v0 - min(v0, kBaseBelow), 0xffffffffu - kFastSpan + 1u);
+        bool ok = count_values(sm, in, N, base, vmin, vmax);
+        if (!ok && vmax - vmin < kFastSpan) {
+            base = vmin;
+            ok = count_values(sm, in, N, base, vmin, vmax);
         }
+        if (ok && count_runs(sm, in, N, base, vmin, vmax, rt, desc + s, labB + off, sweep_stats)) return;
+        // too many distinct values (or too wide a span) for the counting path: radix sort
         __syncthreads();
     }
+    digit0_minmax(sm, in, N, vmin, vmax);
     const int bits = vmax ? 32 - __clz(vmax) : 0;
     const int passes = max(1, (bits + 7) / 8);
     const bool comp = vmax < 65536u;

@@ -1,11 +1,12 @@
-"""Batching machinery on the GPU: CUDA-graph replay and the scan-tile autotuner.
+"""Batching machinery on the GPU: CUDA-graph replay, the scan-tile autotuner, host input.
 
-Neither changes any result: graph replays and tuned tiles must give exactly the answers of direct
-calls with the default tile (which are checked against the oracle elsewhere).
+None of them changes any result: graph replays, tuned tiles and chunked host input must give the
+oracle's answers (k, num, den bit-identical, p within 1e-12 relative) and those of direct calls.
 """
 import numpy as np
 import pytest
 
+import oracle
 import paper_2511_05958_b300 as mt4g
 import synth
 
@@ -31,6 +32,14 @@ def _same(x, y):
         assert np.array_equal(a, c)
 
 
+def _oracle_same(b, got, alpha=1e-6, min_seg=1, max_cp=16):
+    """got = [count, idx, dnum, dden, p] of a segmentation against the oracle's."""
+    _, ocnt, oidx, onum, oden, op = oracle.ks_segment(b.samples, b.offsets, b.steps, alpha, min_seg, max_cp,
+                                                      nthreads=8)
+    _same([ocnt, oidx, onum, oden], got[:4])
+    assert (np.abs(got[4] - op) <= 1e-12 * np.abs(op)).all()
+
+
 def test_graph_replay_matches_direct_calls(eng):
     b = synth.generate(2, 41, 64)
     d = mt4g.to_device_samples(b.samples)
@@ -40,6 +49,7 @@ def test_graph_replay_matches_direct_calls(eng):
     _same(ref, g1)
     r2, g2 = _seg(eng, d, b, out=r1)  # replayed (same pointers and tables)
     _same(ref, g2)
+    _oracle_same(b, g2)
     # new data behind the same pointer: the replay reads it
     b2 = synth.generate(2, 42, 64)
     d.copy_(mt4g.to_device_samples(b2.samples))
@@ -47,6 +57,7 @@ def test_graph_replay_matches_direct_calls(eng):
     eng.set_option(mt4g.OPT_GRAPH, 0)
     _, ref3 = _seg(eng, d, b2)
     _same(ref3, g3)
+    _oracle_same(b2, g3)
     # a different shape is captured again
     eng.set_option(mt4g.OPT_GRAPH, 1)
     b3 = synth.generate(3, 2, 40)
@@ -55,6 +66,7 @@ def test_graph_replay_matches_direct_calls(eng):
     eng.set_option(mt4g.OPT_GRAPH, 0)
     _, ref4 = _seg(eng, d3, b3)
     _same(ref4, g4)
+    _oracle_same(b3, g4)
 
 
 def test_graph_replay_scan_and_learned(eng):
@@ -89,6 +101,7 @@ def test_autotune_keeps_results_and_roundtrips(eng, tmp_path):
     assert tiles <= {1, 2, 4, mt4g.SCAN_SWEEP}
     _, tuned = _seg(eng, d, bb)
     _same(ref, tuned)
+    _oracle_same(bb, tuned)
     path = str(tmp_path / "tune.txt")
     eng.autotune_save(path)
     e2 = mt4g.Engine(0)
@@ -114,6 +127,7 @@ def test_host_input_chunks_match_device_input(eng):
             for chunk in (1, 3 * 65536 + 1, 10**9):
                 r = eng.ks_segment_host(host, b.offsets, b.steps, 1e-6, 1, 16, mode=mode, chunk_samples=chunk)
                 _same(ref, [t.cpu().numpy() for t in r[1:6]])
+            _oracle_same(b, [t.cpu().numpy() for t in r[1:6]])
         # numpy input, ragged series, a capacity overflow in one chunk only
         rng = np.random.default_rng(5)
         series = [rng.integers(0, 50, size=(int(rng.integers(2, 60)), int(rng.integers(1, 9))), dtype=np.uint32)
@@ -126,6 +140,7 @@ def test_host_input_chunks_match_device_input(eng):
         assert hr.rc == mt4g.ECAPACITY
         for a, c in zip(full[1:6], hr[1:6]):
             assert np.array_equal(a.cpu().numpy(), c.cpu().numpy())
+        _oracle_same(bb, [t.cpu().numpy() for t in hr[1:6]], max_cp=8)
     finally:
         eng.set_option(mt4g.OPT_CONF_MIN_PPM, 900000)
 

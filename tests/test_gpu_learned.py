@@ -211,7 +211,7 @@ def test_training_reduces_loss(eng):
 
 def _segment(eng, b, mode, alpha=1e-6, min_seg=1, max_cp=16):
     r = eng.ks_segment(mt4g.to_device_samples(b.samples), b.offsets, b.steps, alpha, min_seg, max_cp, mode=mode)
-    return r.rc, [t.cpu().numpy() for t in r[1:]]
+    return r.rc, [t.cpu().numpy() for t in r[1:7]]
 
 
 def _assert_same(full, learned):
@@ -248,6 +248,8 @@ def test_learned_mode_equals_full_on_three_level_series(eng, seed):
     sb = synth.from_arrays([b.series(s) for s in sample])
     orc, ocnt, oidx, onum, oden, op = oracle.ks_segment(sb.samples, sb.offsets, sb.steps, 1e-6, 1, 16, nthreads=8)
     assert np.array_equal(learned[1][0][sample], ocnt) and np.array_equal(learned[1][1][sample], oidx)
+    assert np.array_equal(learned[1][2][sample], onum) and np.array_equal(learned[1][3][sample], oden)
+    assert (np.abs(learned[1][4][sample] - op) <= 1e-12 * np.abs(op)).all()
 
 
 def test_learned_mode_fallback_threshold(eng):

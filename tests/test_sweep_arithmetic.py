@@ -4,10 +4,12 @@ The CUDA kernels cannot run here; these tests replay, in plain Python integers r
 the way the kernels' registers wrap, the formulation the kernels use, and compare it with the
 definition g_k = max_x |H c_L(x) - a C(x)| (Sec. II-C-1, Sec. IV-B-1 (4)) evaluated by brute force.
 What is pinned:
-  - the per-lane blocks of runs (R even, R = 2 mod 4 from 8 on, at most 32 blocks),
-  - values accumulated relative to the run before each block, with the block's offset taken from
-    a scan of the blocks' sums of l afterwards,
-  - pairs past a block's end evaluated with l = 0 and the block's last C (no effect),
+  - the per-lane blocks of runs: R = ceil(U'/32) rounded up to a multiple of 4 (at least 4), the
+    same for all 32 lanes, positions at or past U' padded with l = 0 and C = N,
+  - the padded layout (lane stride R or R + 4 words) and the run -> layout position map, within
+    the stage's 32 (48 + 4) words,
+  - values accumulated relative to the run before each block, four runs per 16-byte load, with the
+    block's offset taken from a scan of the blocks' sums of l afterwards,
   - the counting sort's run table, run indices and nearest-rank order statistics.
 The GPU parity tests (-m gpu) compare the kernels themselves with the oracle.
 """
@@ -34,35 +36,37 @@ def brute_g(x, m, lo, hi):
     return out
 
 
+MAX_R, STAGE_WORDS = 48, 32 * (48 + 4)
+
+
 def lane_blocks(Uc):
-    Ue = Uc + (Uc & 1)
-    R = (Ue + 31) // 32
-    R += R & 1
-    if R >= 8 and R % 4 == 0:
-        R += 2
-    return Ue, R, [(min(L * R, Ue), min(min(L * R, Ue) + R, Ue)) for L in range(32)]
+    """Block size R, lane stride Rs and each lane's first run."""
+    R = max(4, -(-((Uc + 31) // 32) // 4) * 4)
+    Rs = R if R % 8 == 4 else R + 4
+    return R, Rs, [L * R for L in range(32)]
 
 
 def sweep_g(x, m, lo, hi, A, B):
-    """The sweep's arithmetic: compact runs, lane blocks, relative values, block-sum scan."""
+    """The sweep's arithmetic: compact runs, padded lane blocks, relative values, block-sum scan."""
     dv = np.unique(x)
     rk = np.searchsorted(dv, x)
     H = hi - lo
     cnt = np.bincount(rk[lo * m:hi * m], minlength=len(dv))
     keep = np.nonzero(cnt)[0]
-    mp = np.full(len(dv), -1)
-    mp[keep] = np.arange(len(keep))
     Uc = len(keep)
-    Ue, R, blocks = lane_blocks(Uc)
-    assert R <= 50 and all(b1 - b0 <= R and (b1 - b0) % 2 == 0 for b0, b1 in blocks)
+    R, Rs, firsts = lane_blocks(Uc)
+    assert R <= MAX_R and 32 * Rs <= STAGE_WORDS
+    pos = np.full(len(dv), -1)
+    pos[keep] = [(ci // R) * Rs + ci % R for ci in range(Uc)]
+    assert pos.max() < 32 * Rs and len(set(pos[keep].tolist())) == Uc
     C = [int(c) % M32 for c in np.cumsum(cnt[keep])]
-    if Uc & 1:
-        C.append(C[-1])  # padding run: l = 0, same C
-    l = [0] * Ue
+    N = C[-1]
+    assert N == m * H
+    l = [0] * (32 * Rs)
 
     def add_step(t):
         for j in range(m):
-            c = mp[rk[t * m + j]]
+            c = pos[rk[t * m + j]]
             l[c] = (l[c] + H) % M32
 
     for t in range(lo, A):
@@ -71,31 +75,22 @@ def sweep_g(x, m, lo, hi, A, B):
     for k in range(A, B + 1):
         a = k - lo
         sums, ext = [], []
-        for b0, b1 in blocks:
-            Cb = C[b0 - 1] if b0 > 0 else 0
-            clast = C[b1 - 1] if b1 > b0 else 0
+        for L, b0 in enumerate(firsts):
+            Cb = 0 if b0 == 0 else (C[b0 - 1] if b0 <= Uc else N)
+            Cr = [C[b0 + j] if b0 + j < Uc else N for j in range(R)]
             h0 = (a * Cb) % M32
             hc, mx, mn = h0, -(1 << 31), (1 << 31) - 1
-            npair = (b1 - b0) // 2
-            for g in range(0, 25, 4):  # groups of four pairs, as loaded
-                if g >= npair:
-                    break
-                for j in range(g, min(g + 4, 25)):
-                    lo2 = (l[b0 + 2 * j], l[b0 + 2 * j + 1]) if j < npair else (0, 0)
-                    c0 = C[b0 + 2 * j] if b0 + 2 * j < b1 else clast
-                    c1 = C[b0 + 2 * j + 1] if b0 + 2 * j + 1 < b1 else clast
-                    hc = (hc + lo2[0]) % M32
-                    v0 = s32(hc + (M32 - a) * c0)
-                    hc = (hc + lo2[1]) % M32
-                    v1 = s32(hc + (M32 - a) * c1)
-                    mx, mn = max(mx, v0, v1), min(mn, v0, v1)
+            for q in range(R // 4):  # one 16-byte load: four runs
+                for j in range(4 * q, 4 * q + 4):
+                    hc = (hc + l[L * Rs + j]) % M32
+                    v = s32(hc + (M32 - a) * Cr[j])
+                    mx, mn = max(mx, v), min(mn, v)
             sums.append((hc - h0) % M32)
-            ext.append((Cb, mx, mn, npair > 0))
+            ext.append((Cb, mx, mn))
         carry, g = 0, 0
-        for blk, (Cb, mx, mn, nonempty) in zip(sums, ext):
+        for blk, (Cb, mx, mn) in zip(sums, ext):
             vs = (carry - a * Cb) % M32
-            if nonempty:
-                g = max(g, s32(vs + mx % M32), -s32(vs + mn % M32), 0)
+            g = max(g, s32(vs + mx % M32), -s32(vs + mn % M32), 0)
             carry = (carry + blk) % M32
         res[k] = g
         if k < B:
@@ -123,16 +118,18 @@ def test_sweep_arithmetic_matches_definition(seed):
 
 
 def test_lane_blocks_cover_every_size():
-    """Blocks tile [0, Ue) in at most 32 lanes, R <= 50, and, from R = 8 on, a half warp's 8-byte
-    pair loads fall on distinct banks (R = 2 mod 4)."""
+    """For every U' up to the sweep's 1536 runs: 32 blocks of R runs cover [0, U'), R <= 48 is a
+    multiple of 4, the layout fits the stage, and the eight lanes of a quarter warp start their
+    16-byte loads on eight different four-bank groups (lane stride Rs = 4 mod 8)."""
     for Uc in range(1, 1537):
-        Ue, R, blocks = lane_blocks(Uc)
-        covered = [c for b0, b1 in blocks for c in range(b0, b1)]
-        assert covered == list(range(Ue))
-        assert R <= 50
-        if R >= 8:
-            banks = {((L * R) // 2) % 16 for L in range(16)}
-            assert len(banks) == 16
+        R, Rs, firsts = lane_blocks(Uc)
+        assert R % 4 == 0 and 4 <= R <= MAX_R and 32 * R >= Uc and 32 * Rs <= STAGE_WORDS
+        assert R == 4 or 32 * (R - 4) < Uc  # no larger than needed
+        assert Rs % 8 == 4
+        for q in range(R // 4):
+            for L0 in range(0, 32, 8):
+                groups = {((L * Rs + 4 * q) // 4) % 8 for L in range(L0, L0 + 8)}
+                assert len(groups) == 8
 
 
 def test_counting_sort_tables():

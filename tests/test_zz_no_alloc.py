@@ -1,14 +1,16 @@
-"""The allocation-free scan entry point (mt4g_ks_scan_noalloc) against mt4g_ks_scan.
+"""The allocation-free scan entry point (mt4g_ks_scan_noalloc) against mt4g_ks_scan and the oracle.
 
-Callers that cannot allocate (device memory owned by another pool or arena, a stream capture in
-progress, allocation forbidden after start-up) use the no-allocation variant; its results must be
-those of the ordinary entry point: identical k and exact D, p within 1e-12 relative.  Two calls in
-a row check that the second is not disturbed by what the first left in the shared static array.
-This file is collected last so that a stop at the first failure has already run every other test.
+Callers that cannot allocate device memory (code inside a pool or arena someone else owns, a
+process that forbids allocation after start-up) use the no-allocation variant; its results must be
+those of the ordinary entry point and of the oracle: identical k and exact D, p within 1e-12
+relative.  Two calls in a row check that the second is not disturbed by what the first left in the
+shared static array.  This file is collected last so that a stop at the first failure has already
+run every other test.
 """
 import numpy as np
 import pytest
 
+import oracle
 import paper_2511_05958_b300 as mt4g
 import synth
 
@@ -49,6 +51,9 @@ def test_noalloc_matches_ks_scan_twice_in_a_row():
     eng = mt4g.Engine(0)
     for b in _batches():
         ref = [t.cpu().numpy() for t in eng.ks_scan(mt4g.to_device_samples(b.samples), b.offsets, b.steps)]
+        ok, onum, oden, op = oracle.ks_scan(b.samples, b.offsets, b.steps, nthreads=8)
+        assert np.array_equal(ref[0], ok) and np.array_equal(ref[1], onum) and np.array_equal(ref[2], oden)
+        assert (np.abs(ref[3] - op) <= 1e-12 * np.abs(op)).all()
         for _ in range(2):
             k, num, den, p = _noalloc(b)
             assert np.array_equal(k, ref[0]) and np.array_equal(num, ref[1]) and np.array_equal(den, ref[2])
@@ -57,14 +62,22 @@ def test_noalloc_matches_ks_scan_twice_in_a_row():
 
 
 def test_noalloc_rejects_sizes_beyond_its_limits():
+    """Beyond its stated limits the entry point returns MT4G_EINVAL before any GPU work; the
+    binding rejects buffers too small for the tables it is given."""
     import torch
-    d = torch.zeros(16, dtype=torch.int32, device="cuda")
-    out = mt4g.ScanResult(torch.zeros(1, dtype=torch.int32, device="cuda"),
-                          torch.zeros(1, dtype=torch.int64, device="cuda"),
-                          torch.zeros(1, dtype=torch.int64, device="cuda"),
-                          torch.zeros(1, dtype=torch.float64, device="cuda"))
-    too_many = mt4g.NOALLOC_MAX_SAMPLES + 2
-    assert mt4g.ks_scan_noalloc(d, np.array([0, too_many], np.int64), np.array([2], np.int32), out) == mt4g.EINVAL
     S = mt4g.NOALLOC_MAX_SERIES + 1
+    too_many = mt4g.NOALLOC_MAX_SAMPLES + 2
+    d = torch.zeros(max(too_many, 2 * S), dtype=torch.int32, device="cuda")
+
+    def outs(n):
+        return mt4g.ScanResult(torch.zeros(n, dtype=torch.int32, device="cuda"),
+                               torch.zeros(n, dtype=torch.int64, device="cuda"),
+                               torch.zeros(n, dtype=torch.int64, device="cuda"),
+                               torch.zeros(n, dtype=torch.float64, device="cuda"))
+    assert mt4g.ks_scan_noalloc(d, np.array([0, too_many], np.int64), np.array([2], np.int32), outs(1)) == mt4g.EINVAL
     offs = np.arange(S + 1, dtype=np.int64) * 2
-    assert mt4g.ks_scan_noalloc(d, offs, np.full(S, 2, np.int32), out) == mt4g.EINVAL
+    assert mt4g.ks_scan_noalloc(d, offs, np.full(S, 2, np.int32), outs(S)) == mt4g.EINVAL
+    with pytest.raises(mt4g.Mt4gError):
+        mt4g.ks_scan_noalloc(d[:8], np.array([0, 16], np.int64), np.array([2], np.int32), outs(1))
+    with pytest.raises(mt4g.Mt4gError):
+        mt4g.ks_scan_noalloc(d, np.array([0, 16, 32], np.int64), np.array([2, 2], np.int32), outs(1))
