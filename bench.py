@@ -52,11 +52,11 @@ LAUNCHES = {False: 4, True: 14}  # our kernels per call (plain / learned)
 RECIPES = {2: "synth recipe 2 (T=512, m=128, levels 35/300/800/1100, 0.5% outliers)",
            3: "synth recipe 3 (T 32..4096, m 8..256, 0-4 level ratios 1.01..30, Pareto tails)"}
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch, per series, from the ncu
-# capture summarised in profiles/sort_series_kernel_512x512x128.md (512 series of recipe 2); keyed
-# by (workload, stage) and scaled by the number of series.  The learned workload runs the same sort
-# kernel.  Only kernels captured as they are now appear here; the others (the queue kernels,
-# changed since their captures) report null.
-NCU_TRAFFIC_PER_SERIES = {("plain", "sort"): 196.957184e6 / 512, ("learned", "sort"): 196.957184e6 / 512}
+# capture summarised in profiles/sort_series_kernel_4096x512x128.md (4096 series of recipe 2); keyed
+# by (workload, stage) and scaled by the number of series.  The plain workload runs the same sort
+# kernel on the same distribution.  Only kernels captured as they are now appear here; the others
+# report null.
+NCU_TRAFFIC_PER_SERIES = {("plain", "sort"): 2136.736784e6 / 4096, ("learned", "sort"): 2136.736784e6 / 4096}
 STAGES = ["upload", "sort", "proposals", "queue", "collect"]
 
 

@@ -90,6 +90,12 @@ extern "C" {
                                     scan relies on (run table from 0 to N, strictly increasing;
                                     labels < T; labels non-decreasing inside a run); a violation
                                     makes mt4g_wait return MT4G_ECHECK.  Off by default. */
+#define MT4G_OPT_SWEEP_SKIP 9    /* 1: the run sweep skips splits that an exact bound excludes: a step
+                                    moves m samples, so |g_(k+j) - g_k| <= j m H (g = max_x |H c_L -
+                                    (k - lo) C|); a split whose bound from the last evaluated split
+                                    gives a D strictly below the best D so far is not evaluated (its
+                                    samples still move).  The answers are those of the full scan;
+                                    mt4g_last_work counts only the evaluated pairs.  Off by default. */
 
 typedef struct mt4g_ctx mt4g_ctx;
 

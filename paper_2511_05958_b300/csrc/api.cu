@@ -74,6 +74,7 @@ struct mt4g_ctx {
     int ring_count = 0;
 
     bool checks = false;  // MT4G_OPT_CHECKS: consistency check of the sort's output
+    bool sweep_skip = false;  // MT4G_OPT_SWEEP_SKIP: exact bound skipping in the run sweep
 
     // CUDA-graph replay of identical calls (MT4G_OPT_GRAPH)
     bool use_graph = false;
@@ -147,7 +148,8 @@ struct Plan {
     std::vector<int32_t> sort_order;   // series by size, largest first
     std::vector<int32_t> qorder;       // series by scan cost (T^2 m), costliest first
     std::vector<int64_t> item_base;    // first queue slot of the top-level slices of qorder[i]
-    int64_t n_init = 0;                // top-level slices
+    int64_t n_init = 0;                // top-level items
+    int32_t top_parts = 1;             // parts of each top-level run-sweep segment
     unsigned long long cap = 0;
     bool learned = false;              // items are pushed by the learned init kernel
     bool use_sweep = false;            // run-sweep series present: ranks from the sort, sweep kernel
@@ -329,11 +331,20 @@ int make_plan(mt4g_ctx *ctx, const int64_t *offsets, const int32_t *steps, int64
             return ca > cb;
         });
     }
+    // top-level run-sweep segments are cut into parts when the launch has more warps than
+    // such series (a small batch), so that no warp starts idle
+    int64_t n_sweep = 0;
+    for (const auto &d : P.desc) n_sweep += d.kpt == 0;
+    if (n_sweep > 0) {
+        const int64_t warps = (int64_t)ctx->grid_sweep * (kSweepThreads / 32);
+        P.top_parts = (int32_t)std::max<int64_t>(1, std::min<int64_t>(kSweepMaxParts, warps / n_sweep));
+    }
     P.item_base.resize(S);
     int64_t nb = 0;
     for (int64_t i = 0; i < S; i++) {
         P.item_base[i] = nb;
-        nb += seg_chunks(P.desc[P.qorder[i]].T, min_seg, P.desc[P.qorder[i]].kpt);
+        const SeriesDesc &d = P.desc[P.qorder[i]];
+        nb += d.kpt == 0 ? sweep_parts(d.T, min_seg, P.top_parts) : seg_chunks(d.T, min_seg, d.kpt);
     }
     P.n_init = nb;
     // slices of the children of accepted splits: a split of a segment adds at most
@@ -490,8 +501,8 @@ int enqueue_pipeline(mt4g_ctx *ctx, const uint32_t *samples, Plan &P, RunParams 
     CUDA_TRY(ctx, staged(ctx, us));
     CUDA_TRY(ctx, uploads_done(ctx, us, st));
     if (!P.learned)
-        CUDA_TRY(ctx, launch_init_items(B.desc, B.qorder, B.item_base, P.S, P.min_seg, B.items, B.ready, B.gcount,
-                                        epoch, st));
+        CUDA_TRY(ctx, launch_init_items(B.desc, B.qorder, B.item_base, P.S, P.min_seg, P.top_parts, B.items,
+                                        B.ready, B.gcount, epoch, st));
     mark(ctx, 1, st);
 
     const uint32_t *sort_in = samples;
@@ -522,6 +533,9 @@ int enqueue_pipeline(mt4g_ctx *ctx, const uint32_t *samples, Plan &P, RunParams 
     R.cp_den = B.cp_den;
     R.cp_p = B.cp_p;
     R.cp_crit = B.cp_crit;
+    R.sweep_warps = ctx->grid_sweep * (kSweepThreads / 32);
+    R.sweep_skip = ctx->sweep_skip ? 1 : 0;
+    R.top_parts = P.top_parts;
     return (int)epoch;  // >= 0
 }
 
@@ -646,6 +660,10 @@ int mt4g_set_option(mt4g_ctx *c, int option, int64_t value) {
     }
     if (option == MT4G_OPT_CHECKS) {
         c->checks = value != 0;
+        return MT4G_OK;
+    }
+    if (option == MT4G_OPT_SWEEP_SKIP) {
+        c->sweep_skip = value != 0;
         return MT4G_OK;
     }
     if (option == MT4G_OPT_WINDOWS) {
@@ -875,6 +893,7 @@ uint64_t call_key(const mt4g_ctx *ctx, int entry, const void *samples, const int
     h = fnv_val(h, ctx->conf_min);
     h = fnv_val(h, ctx->forced_kpt);
     h = fnv_val(h, ctx->checks);
+    h = fnv_val(h, ctx->sweep_skip);
     h = fnv_val(h, ctx->cnn_version);
     for (int i = 0; i < n_outs; i++) h = fnv_val(h, outs[i]);
     if (S > 0 && offsets && steps) {

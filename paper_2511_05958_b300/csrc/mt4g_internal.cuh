@@ -150,6 +150,9 @@ struct RunParams {
     int32_t half;               // window slice covers [c - half, c - half + 31]
     const int32_t *fallback;    // [S]: 1 = the series takes the plain path
     CertRecord *recs;
+    int32_t sweep_warps;        // warps of the launch: the sweep's parts per segment follow from them
+    int32_t sweep_skip;         // 1: the run sweep skips splits by the exact bound (MT4G_OPT_SWEEP_SKIP)
+    int32_t top_parts;          // parts of a top-level run-sweep segment (planned on the host)
 };
 
 // Number of slices of a segment of H steps (0 if it cannot be split).
@@ -158,6 +161,33 @@ __host__ __device__ inline int32_t seg_chunks(int32_t H, int32_t min_seg, int32_
     if (kpt == 0) return nk <= 0 ? 0 : 1;  // run sweep: the whole segment
     const int32_t w = 32 * kpt;
     return nk <= 0 ? 0 : (nk + w - 1) / w;
+}
+
+// Run-sweep items.  A segment the sweep takes is one item, or, when warps would otherwise be
+// idle (small batches; the end of a run), up to kSweepMaxParts items that sweep consecutive
+// ranges of its splits, each replaying the earlier steps' sample moves first; the group's last
+// member combines their best splits.  WorkItem.rec = kSweepItem marks them, k0 .. klim is the
+// part's split range.
+constexpr int32_t kSweepItem = -2;
+constexpr int kSweepMaxParts = 8;
+constexpr int kSweepMinPartSplits = 48;
+
+// Parts for a segment of H steps when `want` are wanted (0 if it cannot be split).
+__host__ __device__ inline int32_t sweep_parts(int32_t H, int32_t min_seg, int32_t want) {
+    const int32_t nk = H - 2 * min_seg + 1;
+    if (nk <= 0) return 0;
+    int32_t p = nk / kSweepMinPartSplits;
+    p = p < 1 ? 1 : (p > kSweepMaxParts ? kSweepMaxParts : p);
+    want = want < 1 ? 1 : want;
+    return want < p ? want : p;
+}
+
+// Splits [k0, k1] of part c of np over the splits [A, B] of a segment.
+__host__ __device__ inline void sweep_part_range(int32_t A, int32_t B, int32_t c, int32_t np, int32_t &k0,
+                                                 int32_t &k1) {
+    const int64_t nk = (int64_t)B - A + 1;
+    k0 = A + (int32_t)(nk * c / np);
+    k1 = A + (int32_t)(nk * (c + 1) / np) - 1;
 }
 
 // ---- kernels (launch wrappers live in the .cu files) ----
@@ -170,9 +200,11 @@ cudaError_t launch_sort(const uint32_t *samples, SeriesDesc *desc, const int32_t
                         unsigned long long *sweep_stats, cudaStream_t st);
 
 cudaError_t launch_queue_run(const RunParams &P, int grid, uint32_t epoch, cudaStream_t st);
+// Top-level items: run-sweep series (kpt 0) get top_parts parts (sweep_parts), the others their
+// slices; item_base[i] is the first slot of series qorder[i].
 cudaError_t launch_init_items(const SeriesDesc *desc, const int32_t *qorder, const int64_t *item_base, int64_t S,
-                              int32_t min_seg, WorkItem *items, int32_t *ready, uint32_t *gcount, uint32_t epoch,
-                              cudaStream_t st);
+                              int32_t min_seg, int32_t top_parts, WorkItem *items, int32_t *ready, uint32_t *gcount,
+                              uint32_t epoch, cudaStream_t st);
 cudaError_t launch_init_learned(const RunParams &P, const float *conf, float conf_min, int32_t *fallback_out,
                                 int64_t S, uint32_t epoch, cudaStream_t st);
 int queue_grid(int device);        // CTAs of the slice-only kernel

@@ -175,7 +175,7 @@ extern "C" int mt4g_ks_scan_noalloc(const uint32_t *samples, const int64_t *offs
     uint32_t *gcount = (uint32_t *)(db + L.off_gcount);
     const uint32_t epoch = 1u << 16;
     NA_TRY(launch_init_items(desc, (const int32_t *)(db + L.off_qorder), (const int64_t *)(db + L.off_base), S, 1,
-                             items, ready, gcount, epoch, st));
+                             1, items, ready, gcount, epoch, st));
     NA_TRY(launch_sort(samples, desc, (const int32_t *)(db + L.off_order), S, (uint32_t *)(db + L.off_keyA),
                        (uint32_t *)(db + L.off_keyB), (uint16_t *)(db + L.off_labA), (uint16_t *)(db + L.off_labB),
                        (int32_t *)(db + L.off_runs), nullptr, st));

@@ -135,6 +135,13 @@ __device__ __forceinline__ bool better(int k1, uint64_t g1, int k2, uint64_t g2,
     return k1 < k2;
 }
 
+// 128-bit test x1 * y1 < x2 * y2 for unsigned 64-bit operands.
+__device__ __forceinline__ bool prod_less(uint64_t x1, uint64_t y1, uint64_t x2, uint64_t y2) {
+    const uint64_t h1 = __umul64hi(x1, y1), l1 = x1 * y1;
+    const uint64_t h2 = __umul64hi(x2, y2), l2 = x2 * y2;
+    return h1 < h2 || (h1 == h2 && l1 < l2);
+}
+
 // ---------------------------------------------------------------- scan of one slice
 
 constexpr int kShflMax = 8;  // differentiating samples counted by broadcast; more -> search
@@ -694,20 +701,25 @@ __device__ __forceinline__ void sweep_eval4(const uint4 q, uint32_t c0, uint32_t
     mn = __vimin3_s32(mn, v2, v3);
 }
 
-// Best split (k, g) over A <= k <= B of segment [lo, hi) of a run-sweep series; every lane
-// gets it.  `nonempty` = U', the runs with in-segment samples.
-template <bool VEC>
+// Best split (k, g) over A <= k <= B of segment [lo, hi) of a run-sweep series (A > lo: the
+// samples of steps lo .. A - 1 are moved left first); every lane gets it.  `nonempty` = U', the
+// runs with in-segment samples; `nev` = the splits evaluated.
+//
+// SKIP: exact bound skipping.  Moving one step's m samples changes every v(c) by H s(c) - C(c),
+// s(c) <= m and C(c) <= m H, so |g_{k+j} - g_k| <= j m H.  A split whose bound from the last
+// evaluated split e, g_e + (k - e) m H, gives a D strictly below the best D found so far,
+//     (g_e + (k - e) m H) a_b (H - a_b) < g_b a_k (H - a_k)        (128-bit products),
+// can be neither the argmax nor tie with it, so it is not evaluated; its samples still move.
+template <bool VEC, bool SKIP>
 __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int hi, int A, int B, SweepStage &ss,
-                           int &bk, uint64_t &bg, int &nonempty) {
+                           int &bk, uint64_t &bg, int &nonempty, int &nev) {
     const int lane = threadIdx.x & 31;
     const int U = d.nruns, m = d.m;
     const uint16_t *__restrict__ rk = P.rk + d.off;
     const uint32_t H = (uint32_t)(hi - lo);
     const unsigned lt = lanemask_lt();
 
-    // in-segment samples per series run, into l[r]; during setup map[r] = r, so lc_add counts
-    // at the run itself
-    for (int r = lane; r < U; r += 32) ss.map[r] = (uint16_t)r;
+    // in-segment samples per series run, into l[r]
     if (lo == 0 && hi == d.T) {
         const int32_t *rt = P.runs + d.run_base;
         for (int r = lane; r < U; r += 32) ss.l[r] = (uint32_t)(__ldg(rt + r + 1) - __ldg(rt + r));
@@ -727,10 +739,12 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
 #pragma unroll
                 for (int q = 0; q < 8; q++) {
                     const bool act = e0 + 128 * q + 4 * lane < e1;
-                    lc_add(ss, x8[q].x & 0xffffu, 1u, act);
-                    lc_add(ss, x8[q].x >> 16, 1u, act);
-                    lc_add(ss, x8[q].y & 0xffffu, 1u, act);
-                    lc_add(ss, x8[q].y >> 16, 1u, act);
+                    if (act) {
+                        atomicAdd(&ss.l[x8[q].x & 0xffffu], 1u);
+                        atomicAdd(&ss.l[x8[q].x >> 16], 1u);
+                        atomicAdd(&ss.l[x8[q].y & 0xffffu], 1u);
+                        atomicAdd(&ss.l[x8[q].y >> 16], 1u);
+                    }
                 }
             }
         } else {
@@ -742,7 +756,8 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
                     r16[q] = e < e1 ? (uint32_t)__ldg(rk + e) : 0u;
                 }
 #pragma unroll
-                for (int q = 0; q < 16; q++) lc_add(ss, r16[q], 1u, e0 + 32 * q + lane < e1);
+                for (int q = 0; q < 16; q++)
+                    if (e0 + 32 * q + lane < e1) atomicAdd(&ss.l[r16[q]], 1u);
             }
         }
     }
@@ -798,57 +813,146 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
         sweep_apply_step<VEC>(ss, rk, t, m, H, lane, buf);
     }
     const uint4 *lq = reinterpret_cast<const uint4 *>(&ss.l[lane * Rs]);
-    StepBuf<VEC> nxt;
+    // run indices two steps ahead (global loads in flight over two splits); the layout
+    // positions of step k's samples are looked up at the top of split k and used by its moves
+    // at the end, so the lookups' latency is spent under the evaluation
+    StepBuf<VEC> nxt, nxt2;
     sweep_load_step<VEC>(rk, A, m, lane, nxt);
+    if (A + 1 <= B) sweep_load_step<VEC>(rk, A + 1, m, lane, nxt2);
     bk = kNoK;
     bg = 0;
     uint32_t gk = 0;  // g of split kb + lane
     int kb = A;
-    for (int k = A; k <= B; k++) {
-        const StepBuf<VEC> cur = nxt;
-        if (k + 1 <= B) sweep_load_step<VEC>(rk, k + 1, m, lane, nxt);  // in flight during this split
-        __syncwarp();
-        const uint32_t a = (uint32_t)(k - lo), na = 0u - a;
-        const uint32_t h0 = a * Cb;
-        uint32_t hc = h0;
-        int32_t mx = INT_MIN, mn = INT_MAX;
-        // the block in groups of two quads (8 runs); nq is the same for every lane
-#pragma unroll
-        for (int g = 0; g < kSweepMaxR / 8; g++) {
-            if (2 * g >= nq) break;
-            const bool two = 2 * g + 1 < nq;
-            const uint4 q0 = lq[2 * g];
-            uint4 q1 = make_uint4(0u, 0u, 0u, 0u);
-            if (two) q1 = lq[2 * g + 1];
-            sweep_eval4(q0, Cr[8 * g], Cr[8 * g + 1], Cr[8 * g + 2], Cr[8 * g + 3], na, hc, mx, mn);
-            if (two) sweep_eval4(q1, Cr[8 * g + 4], Cr[8 * g + 5], Cr[8 * g + 6], Cr[8 * g + 7], na, hc, mx, mn);
-        }
-        const uint32_t blk = hc - h0;  // sum of l over the block
-        // every lane has read l for split k: step k's samples move left now (reductions the warp
-        // does not wait for), and the warp's results for split k follow in registers
-        __syncwarp();
-        if (k < B) sweep_apply_step<VEC>(ss, rk, k, m, H, lane, cur);
-        uint32_t incl = blk;
+    // The results of split k - 1 (block sum, relative max and min, a C below the block) are
+    // finished in iteration k, while its first loads are in flight: a warp scan of the block
+    // sums, the block's true max and min, the warp maximum of the moduli, and the argmax.
+    uint32_t p_blk = 0, p_h0 = 0;
+    int32_t p_mx = 0, p_mn = 0;
+    auto split_g = [&]() {
+        uint32_t incl = p_blk;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(kFull, incl, o);
             if (lane >= o) incl += y;
         }
-        const uint32_t vs = (incl - blk) - h0;  // v_k at the run before the block
-        const int32_t bmax = (int32_t)(vs + (uint32_t)mx), bmin = (int32_t)(vs + (uint32_t)mn);
+        const uint32_t vs = (incl - p_blk) - p_h0;  // v at the run before the block
+        const int32_t bmax = (int32_t)(vs + (uint32_t)p_mx), bmin = (int32_t)(vs + (uint32_t)p_mn);
         const uint32_t gl = max((uint32_t)max(bmax, 0), (uint32_t)max(-bmin, 0));
-        const uint32_t g = __reduce_max_sync(kFull, gl);
-        if (lane == k - kb) gk = g;
-        if (k - kb == 31 || k == B) {
+        return __reduce_max_sync(kFull, gl);
+    };
+    // without skipping the argmax is taken 32 splits at a time (lane j holds split kb + j)
+    auto finish = [&](int kp) {
+        const uint32_t g = split_g();
+        if (lane == kp - kb) gk = g;
+        if (kp - kb == 31 || kp == B) {
             const int kk = kb + lane;
-            if (kk <= k && better(kk, (uint64_t)gk, bk, bg, lo, hi)) {
+            if (kk <= kp && better(kk, (uint64_t)gk, bk, bg, lo, hi)) {
                 bk = kk;
                 bg = gk;
             }
-            kb = k + 1;
+            kb = kp + 1;
+        }
+    };
+    // with skipping the best is kept current (the same on every lane)
+    int e = -1;       // last evaluated split
+    uint64_t ge = 0;  // its g
+    bool pev = false;  // split k - 1 was evaluated
+    nev = 0;
+    auto finish_now = [&](int kp) {
+        const uint32_t g = split_g();
+        if (better(kp, (uint64_t)g, bk, bg, lo, hi)) {
+            bk = kp;
+            bg = g;
+        }
+        e = kp;
+        ge = g;
+    };
+    const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
+    for (int k = A; k <= B; k++) {
+        const StepBuf<VEC> cur = nxt;
+        uint32_t pos0 = 0, pos1 = 0, pos2 = 0, pos3 = 0;
+        if (VEC && 4 * lane < m) {
+            pos0 = ss.map[cur.v[0] & 0xffffu];
+            pos1 = ss.map[cur.v[0] >> 16];
+            pos2 = ss.map[cur.v[1] & 0xffffu];
+            pos3 = ss.map[cur.v[1] >> 16];
+        }
+        nxt = nxt2;
+        if (k + 2 <= B) sweep_load_step<VEC>(rk, k + 2, m, lane, nxt2);
+        __syncwarp();
+        // the first group of the block (two quads, 8 runs) while split k - 1 is finished
+        uint4 q0 = lq[0], q1 = zero4;
+        if (nq > 1) q1 = lq[1];
+        bool ev = true;  // split k is evaluated (the same on every lane)
+        if constexpr (SKIP) {
+            if (pev) finish_now(k - 1);
+            if (e >= 0) {
+                const uint64_t ub = ge + (uint64_t)(k - e) * (uint64_t)m * (uint64_t)H;
+                const uint64_t db = (uint64_t)(bk - lo) * (uint64_t)(hi - bk);
+                const uint64_t dk = (uint64_t)(k - lo) * (uint64_t)(hi - k);
+                ev = !prod_less(ub, db, bg, dk);
+            }
+            pev = ev;
+        } else {
+            if (k > A) finish(k - 1);
+        }
+        if (ev) {
+            nev++;
+            const uint32_t a = (uint32_t)(k - lo), na = 0u - a;
+            const uint32_t h0 = a * Cb;
+            uint32_t hc = h0;
+            int32_t mx = INT_MIN, mn = INT_MAX;
+            // the block in groups of two quads, the next group's loads issued before the
+            // current group is evaluated; nq is the same for every lane
+#pragma unroll
+            for (int g = 0; g < kSweepMaxR / 8; g++) {
+                if (2 * g >= nq) break;
+                uint4 n0 = zero4, n1 = zero4;
+                if (2 * g + 2 < nq) n0 = lq[2 * g + 2];
+                if (2 * g + 3 < nq) n1 = lq[2 * g + 3];
+                sweep_eval4(q0, Cr[8 * g], Cr[8 * g + 1], Cr[8 * g + 2], Cr[8 * g + 3], na, hc, mx, mn);
+                if (2 * g + 1 < nq)
+                    sweep_eval4(q1, Cr[8 * g + 4], Cr[8 * g + 5], Cr[8 * g + 6], Cr[8 * g + 7], na, hc, mx, mn);
+                q0 = n0;
+                q1 = n1;
+            }
+            p_blk = hc - h0;  // sum of l over the block
+            p_h0 = h0;
+            p_mx = mx;
+            p_mn = mn;
+        }
+        // every lane has read l for split k: step k's samples move left now (reductions the warp
+        // does not wait for)
+        __syncwarp();
+        if (k < B) {
+            if constexpr (VEC) {
+                if (4 * lane < m) {
+                    atomicAdd(&ss.l[pos0], H);
+                    atomicAdd(&ss.l[pos1], H);
+                    atomicAdd(&ss.l[pos2], H);
+                    atomicAdd(&ss.l[pos3], H);
+                }
+                const uint16_t *src = rk + (int64_t)k * m;
+                for (int j0 = 128; j0 < m; j0 += 128) {
+                    const bool a2 = j0 + 4 * lane < m;
+                    uint2 x = make_uint2(0u, 0u);
+                    if (a2) x = __ldg(reinterpret_cast<const uint2 *>(src + j0) + lane);
+                    lc_add(ss, x.x & 0xffffu, H, a2);
+                    lc_add(ss, x.x >> 16, H, a2);
+                    lc_add(ss, x.y & 0xffffu, H, a2);
+                    lc_add(ss, x.y >> 16, H, a2);
+                }
+            } else {
+                sweep_apply_step<VEC>(ss, rk, k, m, H, lane, cur);
+            }
         }
     }
-    warp_best(bk, bg, lo, hi);
+    if constexpr (SKIP) {
+        if (pev) finish_now(B);
+    } else {
+        finish(B);
+        warp_best(bk, bg, lo, hi);
+    }
     __syncwarp();
 }
 
@@ -871,26 +975,60 @@ __device__ __forceinline__ void put_item(const RunParams &P, unsigned long long 
     dst[1] = make_int4(w.kind_nch, w.k0, w.klim, w.rec);
 }
 
+// The full scan of segment [lo, hi) (all lanes of a warp call it with the same arguments):
+// run-sweep items where the sweep takes the segment, else its slices.  The sweep is cut into
+// parts when fewer items are pending than the launch has warps (and the queue is at most half
+// used), so that idle warps share a long segment.
+// want_parts > 0 (the top level of a learned call): that many parts, as the host planned them.
+__device__ void push_plain(const RunParams &P, const SeriesDesc &d, int series, int lo, int hi, uint32_t epoch,
+                           int want_parts) {
+    const int lane = threadIdx.x & 31;
+    const int A = lo + P.min_seg, B = hi - P.min_seg;
+    const int kpt = eff_kpt(P, d, hi - lo);
+    int nch = 0;
+    if (kpt == 0) {
+        int want = want_parts;
+        if (want_parts <= 0 && lane == 0) {
+            want = 1;
+            const long long pend = *(volatile const long long *)&P.q->pending;
+            const unsigned long long tail = *(volatile const unsigned long long *)&P.q->tail;
+            if (tail < P.q->cap / 2 && pend < (long long)P.sweep_warps)
+                want = (int)(P.sweep_warps / (pend > 1 ? pend : 1));
+        }
+        nch = sweep_parts(hi - lo, P.min_seg, __shfl_sync(kFull, want, 0));
+    } else {
+        nch = seg_chunks(hi - lo, P.min_seg, kpt);
+    }
+    unsigned long long base = 0;
+    if (lane == 0) base = reserve_slots(P, nch);
+    base = __shfl_sync(kFull, base, 0);
+    if (base == ~0ull) return;
+    for (int c = lane; c < nch; c += 32) {
+        if (kpt == 0) {
+            int k0, k1;
+            sweep_part_range(A, B, c, nch, k0, k1);
+            put_item(P, base + c, WorkItem{series, lo, hi, c, kPlain | (nch << 8), k0, k1, kSweepItem});
+        } else {
+            put_item(P, base + c, WorkItem{series, lo, hi, c, kPlain | (nch << 8), 0, B, -1});
+        }
+    }
+    if (lane == 0) P.gcount[base] = 0;
+    __threadfence();
+    for (int c = lane; c < nch; c += 32) st_release_u32((uint32_t *)P.ready + base + c, epoch);
+}
+
 // Push the work for segment [lo, hi) (all lanes of a warp call it with the same arguments).
 // Plain series, and learned segments with no window centred at least half/2 inside their
-// splits: the slices of the full scan.  Other learned segments: a probe group of the
-// window slices that reach the segment's splits plus one grid item.
-__device__ __noinline__ void push_segment(const RunParams &P, const SeriesDesc &d, int series, int lo, int hi, uint32_t epoch) {
+// splits: the full scan (push_plain).  Other learned segments: a probe group of the window
+// slices that reach the segment's splits plus one grid item.
+__device__ __noinline__ void push_segment(const RunParams &P, const SeriesDesc &d, int series, int lo, int hi, uint32_t epoch,
+                                          int want_parts = 0) {
     const int lane = threadIdx.x & 31;
     const int A = lo + P.min_seg, B = hi - P.min_seg;
     if (B < A) return;
     const bool learned = P.mode == kRunLearned && !P.fallback[series];
     if (!learned) {
-        const int nch = seg_chunks(hi - lo, P.min_seg, eff_kpt(P, d, hi - lo));
-        unsigned long long base = 0;
-        if (lane == 0) base = reserve_slots(P, nch);
-        base = __shfl_sync(kFull, base, 0);
-        if (base == ~0ull) return;
-        for (int c = lane; c < nch; c += 32)
-            put_item(P, base + c, WorkItem{series, lo, hi, c, kPlain | (nch << 8), 0, B, -1});
-        if (lane == 0) P.gcount[base] = 0;
-        __threadfence();
-        for (int c = lane; c < nch; c += 32) st_release_u32((uint32_t *)P.ready + base + c, epoch);
+        push_plain(P, d, series, lo, hi, epoch, want_parts);
         return;
     }
     // a probe only pays where a window is centred well inside the segment; elsewhere (in
@@ -901,16 +1039,7 @@ __device__ __noinline__ void push_segment(const RunParams &P, const SeriesDesc &
         inner = c >= A + P.half / 2 && c <= B - P.half / 2;
     }
     if (__ballot_sync(kFull, inner) == 0) {
-        const int nch = seg_chunks(hi - lo, P.min_seg, eff_kpt(P, d, hi - lo));
-        unsigned long long base = 0;
-        if (lane == 0) base = reserve_slots(P, nch);
-        base = __shfl_sync(kFull, base, 0);
-        if (base == ~0ull) return;
-        for (int c = lane; c < nch; c += 32)
-            put_item(P, base + c, WorkItem{series, lo, hi, c, kPlain | (nch << 8), 0, B, -1});
-        if (lane == 0) P.gcount[base] = 0;
-        __threadfence();
-        for (int c = lane; c < nch; c += 32) st_release_u32((uint32_t *)P.ready + base + c, epoch);
+        push_plain(P, d, series, lo, hi, epoch, want_parts);
         return;
     }
     if (lane == 0) {
@@ -978,12 +1107,6 @@ __device__ __noinline__ void finish_segment(const RunParams &P, const SeriesDesc
     push_segment(P, d, series, k, hi, epoch);
 }
 
-// 128-bit test x1 * y1 < x2 * y2 for unsigned 64-bit operands.
-__device__ __forceinline__ bool prod_less(uint64_t x1, uint64_t y1, uint64_t x2, uint64_t y2) {
-    const uint64_t h1 = __umul64hi(x1, y1), l1 = x1 * y1;
-    const uint64_t h2 = __umul64hi(x2, y2), l2 = x2 * y2;
-    return h1 < h2 || (h1 == h2 && l1 < l2);
-}
 
 // After a learned segment's probe group: (k, g) is the best exact split among its windows
 // and grid splits.  A gap (a, b) is certified when its bound cannot reach D(k):
@@ -1103,7 +1226,8 @@ __device__ void slice_best(const RunParams &P, const SeriesDesc &d, int lo, int 
 // SWEEP = true adds the run sweep: each warp's shared memory then holds a SweepStage (for
 // up to kSweepMaxRuns runs), launched as CTAs of kSweepThreads; without it, the smaller
 // slice staging allows more resident warps.
-template <bool LEARNED, bool SWEEP>
+// SKIP (with SWEEP) compiles the run sweep with exact bound skipping (MT4G_OPT_SWEEP_SKIP).
+template <bool LEARNED, bool SWEEP, bool SKIP = false>
 __global__ void __launch_bounds__(SWEEP ? kSweepThreads : kScanThreads, SWEEP ? 8 : 4)
     queue_kernel(RunParams P, uint32_t epoch) {
     using Smem = typename std::conditional<SWEEP, WarpSmem, WarpStage>::type;
@@ -1172,21 +1296,24 @@ __global__ void __launch_bounds__(SWEEP ? kSweepThreads : kScanThreads, SWEEP ? 
             bk = gk >= 0 ? gk : kNoK;
             bg = gk >= 0 ? g : 0;
             warp_best(bk, bg, lo, hi);
-        } else if (SWEEP && kind == kPlain && eff_kpt(P, d, hi - lo) == 0) {
+        } else if (SWEEP && kind == kPlain && it.rec == kSweepItem) {
             if constexpr (SWEEP) {
-                SweepStage &ss = *reinterpret_cast<SweepStage *>(&s_stage[warp]);
-                if ((d.off & 3) == 0 && (d.m & 3) == 0)
-                    sweep_best<true>(P, d, lo, hi, A, B, ss, bk, bg, nonempty);
-                else
-                    sweep_best<false>(P, d, lo, hi, A, B, ss, bk, bg, nonempty);
-                my_evals += (unsigned long long)(B - A + 1) * (unsigned long long)nonempty;
-                my_swept++;
+                if (eff_kpt(P, d, hi - lo) == 0) {
+                    SweepStage &ss = *reinterpret_cast<SweepStage *>(&s_stage[warp]);
+                    const bool vec = (d.off & 3) == 0 && (d.m & 3) == 0;
+                    int nev = 0;
+                    if (vec) sweep_best<true, SKIP>(P, d, lo, hi, it.k0, it.klim, ss, bk, bg, nonempty, nev);
+                    else sweep_best<false, SKIP>(P, d, lo, hi, it.k0, it.klim, ss, bk, bg, nonempty, nev);
+                    my_evals += (unsigned long long)nev * (unsigned long long)nonempty;
+                    my_swept += it.chunk == 0;
+                } else {
+                    // a top-level item of a series planned for the sweep that it cannot take (too
+                    // many distinct values, or a wide segment): the segment goes back to the queue
+                    // as slices, once
+                    if (it.chunk == 0) push_segment(P, d, it.series, lo, hi, epoch);
+                    repushed = true;
+                }
             }
-        } else if (kind == kPlain && nch != seg_chunks(hi - lo, P.min_seg, eff_kpt(P, d, hi - lo))) {
-            // a whole-segment item of a run-sweep series that the sweep cannot take (too many
-            // distinct values, or a wide segment): the segment goes back to the queue as slices
-            push_segment(P, d, it.series, lo, hi, epoch);
-            repushed = true;
         } else if (kind == kPlain) {
             const int kpt = eff_kpt(P, d, hi - lo);
             const int k0 = A + it.chunk * 32 * kpt;
@@ -1267,18 +1394,22 @@ __global__ void __launch_bounds__(SWEEP ? kSweepThreads : kScanThreads, SWEEP ? 
 // Expand the top-level slices of every series into the queue, costliest series first.
 __global__ void init_items_kernel(const SeriesDesc *__restrict__ desc, const int32_t *__restrict__ qorder,
                                   const int64_t *__restrict__ item_base, int64_t S, int32_t min_seg,
-                                  WorkItem *items, int32_t *ready, uint32_t *gcount, uint32_t epoch) {
+                                  int32_t top_parts, WorkItem *items, int32_t *ready, uint32_t *gcount,
+                                  uint32_t epoch) {
     const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (i >= S) return;
     const int32_t s = qorder[i];
     const int32_t T = desc[s].T;
-    const int nch = seg_chunks(T, min_seg, desc[s].kpt);
+    const bool sweep = desc[s].kpt == 0;
+    const int nch = sweep ? sweep_parts(T, min_seg, top_parts) : seg_chunks(T, min_seg, desc[s].kpt);
     const int64_t b = item_base[i];
     for (int c = lane; c < nch; c += 32) {
+        int k0 = 0, k1 = T - min_seg;
+        if (sweep) sweep_part_range(min_seg, T - min_seg, c, nch, k0, k1);
         int4 *dst = reinterpret_cast<int4 *>(items + b + c);
         dst[0] = make_int4(s, 0, T, c);
-        dst[1] = make_int4(kPlain | (nch << 8), 0, T - min_seg, -1);
+        dst[1] = make_int4(kPlain | (nch << 8), k0, k1, sweep ? kSweepItem : -1);
         if (c == 0) gcount[b] = 0;
         ready[b + c] = (int32_t)epoch;
     }
@@ -1298,7 +1429,7 @@ __global__ void init_learned_kernel(RunParams P, const float *__restrict__ conf,
     if (lane == 0) fallback_out[s] = (conf[s] < conf_min || swept) ? 1 : 0;
     __syncwarp();
     __threadfence_block();
-    push_segment(P, d, (int)s, 0, d.T, epoch);
+    push_segment(P, d, (int)s, 0, d.T, epoch, P.top_parts);
 }
 
 // One warp per series: gather the flagged steps in ascending order.
@@ -1357,20 +1488,29 @@ int queue_grid(int device) {
 int queue_grid_sweep(int device) {
     int sms = 0, per_sm = 0, per_sm_l = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
+    int per_sm_s = 0, per_sm_ls = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, queue_kernel<false, true>, kSweepThreads, 0) !=
             cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_l, queue_kernel<true, true>, kSweepThreads, 0) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_s, queue_kernel<false, true, true>, kSweepThreads, 0) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_ls, queue_kernel<true, true, true>, kSweepThreads, 0) !=
             cudaSuccess)
         return 0;
-    per_sm = std::min(per_sm, per_sm_l);
+    per_sm = std::min(std::min(per_sm, per_sm_l), std::min(per_sm_s, per_sm_ls));
     return sms * (per_sm > 0 ? per_sm : 1);
 }
 
 cudaError_t launch_queue_run(const RunParams &P, int grid, uint32_t epoch, cudaStream_t st) {
-    if (P.mode == kRunLearned && P.rk)
+    if (P.mode == kRunLearned && P.rk && P.sweep_skip)
+        queue_kernel<true, true, true><<<grid, kSweepThreads, 0, st>>>(P, epoch);
+    else if (P.mode == kRunLearned && P.rk)
         queue_kernel<true, true><<<grid, kSweepThreads, 0, st>>>(P, epoch);
     else if (P.mode == kRunLearned)
         queue_kernel<true, false><<<grid, kScanThreads, 0, st>>>(P, epoch);
+    else if (P.rk && P.sweep_skip)
+        queue_kernel<false, true, true><<<grid, kSweepThreads, 0, st>>>(P, epoch);
     else if (P.rk)
         queue_kernel<false, true><<<grid, kSweepThreads, 0, st>>>(P, epoch);
     else
@@ -1388,12 +1528,12 @@ cudaError_t launch_init_learned(const RunParams &P, const float *conf, float con
 }
 
 cudaError_t launch_init_items(const SeriesDesc *desc, const int32_t *qorder, const int64_t *item_base, int64_t S,
-                              int32_t min_seg, WorkItem *items, int32_t *ready, uint32_t *gcount, uint32_t epoch,
-                              cudaStream_t st) {
+                              int32_t min_seg, int32_t top_parts, WorkItem *items, int32_t *ready, uint32_t *gcount,
+                              uint32_t epoch, cudaStream_t st) {
     if (S <= 0) return cudaSuccess;
     const int warps = 8;
-    init_items_kernel<<<(unsigned)((S + warps - 1) / warps), warps * 32, 0, st>>>(desc, qorder, item_base, S, min_seg,
-                                                                                    items, ready, gcount, epoch);
+    init_items_kernel<<<(unsigned)((S + warps - 1) / warps), warps * 32, 0, st>>>(
+        desc, qorder, item_base, S, min_seg, top_parts, items, ready, gcount, epoch);
     return cudaGetLastError();
 }
 

@@ -189,3 +189,54 @@ def test_uneven_heavy_buckets_full_shape(eng):
     b = synth.from_arrays([synth.generate(3, 2, 1, series_begin=s).series(0) for s in pick])
     assert int(b.offsets[-1]) > 2_000_000
     _check_segment(eng, b, 1e-6, 1, 16, nthreads=8)
+
+
+# ------------------------------------------------------------------ run sweep with bound skipping
+
+def test_sweep_bound_skipping_matches_oracle(eng):
+    """MT4G_OPT_SWEEP_SKIP: splits an exact bound excludes are not evaluated, yet every answer
+    equals the oracle's (heavy ties, ragged shapes, three-level series, reduced mode, a small batch
+    whose segments are cut into parts), and fewer (split, value) pairs are evaluated."""
+    rng = np.random.default_rng(71)
+    b1 = synth.tiny_random(rng, 400, T_range=(2, 40), m_range=(1, 6), vmax=6)
+    series = []
+    for _ in range(50):
+        T = int(rng.integers(2, 900))
+        m = int(rng.integers(1, 9))
+        x = rng.integers(0, int(rng.integers(2, 3000)), size=(T, m))
+        for c in np.sort(rng.choice(np.arange(1, T), size=min(T - 1, 3), replace=False)):
+            x[c:] += int(rng.integers(0, 200))
+        series.append(x.astype(np.uint32))
+    b2 = synth.from_arrays(series)
+    b3 = synth.generate(2, 12, 40)
+    try:
+        for b, alpha in ((b1, 0.05), (b2, 1e-4), (b3, 1e-6)):
+            eng.set_option(mt4g.OPT_SWEEP_SKIP, 0)
+            _check_segment(eng, b, alpha)
+            full = eng.last_work()
+            eng.set_option(mt4g.OPT_SWEEP_SKIP, 1)
+            _check_segment(eng, b, alpha)
+            _check_scan(eng, b)
+            _check_segment(eng, b, alpha, mode=mt4g.MODE_REDUCED)
+            _check_segment(eng, b, alpha, min_seg=3)
+        assert eng.last_sweep()["swept_segments"] > 0
+        eng.set_option(mt4g.OPT_SWEEP_SKIP, 0)
+        _check_segment(eng, b3, 1e-6)
+        full = eng.last_work()
+        eng.set_option(mt4g.OPT_SWEEP_SKIP, 1)
+        _check_segment(eng, b3, 1e-6)
+        assert eng.last_work() < 0.8 * full
+    finally:
+        eng.set_option(mt4g.OPT_SWEEP_SKIP, 0)
+
+
+def test_sweep_bound_skipping_learned_mode(eng):
+    """The learned call with bound skipping in the sweep answers as the full scan and the oracle."""
+    import os
+    b = synth.generate(2, 13, 24)
+    eng.cnn_load(os.path.join(os.path.dirname(__file__), "..", "paper_2511_05958_b300", "weights", "cnn_c2.bin"))
+    try:
+        eng.set_option(mt4g.OPT_SWEEP_SKIP, 1)
+        _check_segment(eng, b, 1e-6, mode=mt4g.MODE_LEARNED)
+    finally:
+        eng.set_option(mt4g.OPT_SWEEP_SKIP, 0)
