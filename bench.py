@@ -15,7 +15,9 @@ Workloads (synthetic series from the seeded generator, resident in HBM before ti
   plain: 1024 series of the same distribution (seed 1), plain full exact segmentation.
   uneven: 16384 series, T ~ U{32..4096}, m in {8,16,64,256}, 0-4 change points with level ratios
       log-uniform in [1.01, 30], 1% Pareto(1.5) tails (seed 2); plain full segmentation, one
-      persistent-kernel launch over the whole batch.
+      persistent-kernel launch over the whole batch with scan tiles per (log2 T, log2 m) bucket
+      from the autotuner (mt4g_autotune, run on the batch before timing), each step one CUDA-graph
+      replay (MT4G_OPT_GRAPH); the stage times come from extra direct calls with the same tiles.
 Every batch is larger than the 126 MB L2, so consecutive steps do not hit in L2.
 
 Prints one JSON line (rank 0).  Under torchrun each rank processes its own batch of the same shape
@@ -52,11 +54,14 @@ LAUNCHES = {False: 4, True: 14}  # our kernels per call (plain / learned)
 RECIPES = {2: "synth recipe 2 (T=512, m=128, levels 35/300/800/1100, 0.5% outliers)",
            3: "synth recipe 3 (T 32..4096, m 8..256, 0-4 level ratios 1.01..30, Pareto tails)"}
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch, per series, from the ncu
-# capture summarised in profiles/sort_series_kernel_4096x512x128.md (4096 series of recipe 2); keyed
-# by (workload, stage) and scaled by the number of series.  The plain workload runs the same sort
-# kernel on the same distribution.  Only kernels captured as they are now appear here; the others
-# report null.
-NCU_TRAFFIC_PER_SERIES = {("plain", "sort"): 2136.736784e6 / 4096, ("learned", "sort"): 2136.736784e6 / 4096}
+# captures summarised under profiles/ (4096 series of recipe 2); keyed by (workload, stage) and
+# scaled by the number of series.  The sort: profiles/sort_series_kernel_4096x512x128.md (the
+# plain workload runs the same kernel on the same distribution).  Only kernels captured as they
+# are now appear here; the others report null.
+# The queue kernels: profiles/queue_kernel_learned_sweep_4096x512x128.md and
+# profiles/queue_kernel_sweep_4096x512x128.md (4096 series each).
+NCU_TRAFFIC_PER_SERIES = {("plain", "sort"): 2136.736784e6 / 4096, ("learned", "sort"): 2136.736784e6 / 4096,
+                          ("learned", "queue"): 2420.595560e6 / 4096, ("plain", "queue"): 2392.773258e6 / 4096}
 STAGES = ["upload", "sort", "proposals", "queue", "collect"]
 
 
@@ -208,6 +213,12 @@ def main():
         eng.cnn_load(WEIGHTS)
     mode = mt4g.MODE_LEARNED if learned else mt4g.MODE_FULL
     stream = torch.cuda.current_stream(dev)
+    graph = args.workload == "uneven"
+    tune_s = None
+    if graph:  # the uneven workload: autotuned tiles per shape bucket, graph replay per step
+        t0 = time.perf_counter()
+        eng.autotune(d_samples, b.offsets, b.steps, stream=stream)
+        tune_s = time.perf_counter() - t0
 
     def barrier():
         if world > 1:
@@ -242,11 +253,24 @@ def main():
         barrier()
         clk = clocks.stop() if clocks else None
         status = eng.wait()
-        stages = eng.stage_times(min(steps, 64))
+        if graph:  # graph replays record no stage times: time direct calls with the same tiles
+            eng.set_option(mt4g.OPT_GRAPH, 0)
+            for _ in range(min(steps, 3) + 1):
+                eng.ks_segment(d_samples, b.offsets, b.steps, ALPHA, 1, MAX_CP, mode=m, stream=stream, out=out,
+                               sync=False)
+            eng.wait()
+            eng.set_option(mt4g.OPT_GRAPH, 1)
+            stages = eng.stage_times(min(steps, 3))
+        else:
+            stages = eng.stage_times(min(steps, 64))
         return max_over_ranks(e0.elapsed_time(e1) / 1e3), out, status, stages, eng.last_work(), clk
 
     clocks = ClockSampler(local)
+    if graph:
+        eng.set_option(mt4g.OPT_GRAPH, 1)
     t_main, out_main, status, stages, evals, clk = timed(mode, args.steps, args.warmup, clocks)
+    if graph:
+        eng.set_option(mt4g.OPT_GRAPH, 0)
     stats = eng.learned_stats() if learned else None
     sweep = eng.last_sweep()
     ranked, counted = sweep["ranked_samples"], sweep["counted_samples"]
@@ -259,6 +283,14 @@ def main():
             "status": int(status), "gpu_launches": LAUNCHES[learned] * args.steps,
             "swept_segments": sweep["swept_segments"], "ranked_samples": ranked, "counted_samples": counted,
             "unswept_series": sweep["unswept_series"]}
+    if graph:
+        tiles = {}
+        for T_, m_ in zip(b.steps, b.m):
+            key = f"T2^{int(T_).bit_length() - 1},m2^{int(m_).bit_length() - 1}"
+            tiles[key] = eng.autotune_get(int(T_), int(m_))
+        line["cuda_graph"] = True
+        line["autotune"] = {"seconds": tune_s, "tiles": dict(sorted(tiles.items())),
+                            "tile_codes": "1/2/4 = groups of 32 splits per work item, 8 = run sweep"}
     if learned:
         res_l = [x.clone() for x in out_main[1:6]]
         fb = out_main[6].clone()

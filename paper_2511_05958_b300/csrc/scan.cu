@@ -727,17 +727,24 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
         for (int r = lane; r < U; r += 32) ss.l[r] = 0;
         __syncwarp();
         const int64_t e1 = (int64_t)hi * m;
-        if constexpr (VEC) {  // rows are 8-byte aligned: four run indices per load, 1024 per round
+        if constexpr (VEC) {  // rows are 8-byte aligned: four run indices per load, 2048 per round
+            // the next round's loads are issued before the current round is counted
             const uint2 *src = reinterpret_cast<const uint2 *>(rk);
-            for (int64_t e0 = (int64_t)lo * m; e0 < e1; e0 += 1024) {
-                uint2 x8[8];
+            uint2 x8[16], y8[16];
+            const int64_t f0 = (int64_t)lo * m;
 #pragma unroll
-                for (int q = 0; q < 8; q++) {
-                    const int64_t e = e0 + 128 * q + 4 * lane;
-                    x8[q] = e < e1 ? __ldg(src + (e >> 2)) : make_uint2(0u, 0u);
+            for (int q = 0; q < 16; q++) {
+                const int64_t e = f0 + 128 * q + 4 * lane;
+                x8[q] = e < e1 ? __ldg(src + (e >> 2)) : make_uint2(0u, 0u);
+            }
+            for (int64_t e0 = f0; e0 < e1; e0 += 2048) {
+#pragma unroll
+                for (int q = 0; q < 16; q++) {
+                    const int64_t e = e0 + 2048 + 128 * q + 4 * lane;
+                    y8[q] = e < e1 ? __ldg(src + (e >> 2)) : make_uint2(0u, 0u);
                 }
 #pragma unroll
-                for (int q = 0; q < 8; q++) {
+                for (int q = 0; q < 16; q++) {
                     const bool act = e0 + 128 * q + 4 * lane < e1;
                     if (act) {
                         atomicAdd(&ss.l[x8[q].x & 0xffffu], 1u);
@@ -745,6 +752,7 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
                         atomicAdd(&ss.l[x8[q].y & 0xffffu], 1u);
                         atomicAdd(&ss.l[x8[q].y >> 16], 1u);
                     }
+                    x8[q] = y8[q];
                 }
             }
         } else {
