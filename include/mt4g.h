@@ -257,7 +257,9 @@ int mt4g_propose(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets,
  * either by the run sweep (MT4G_SCAN_SWEEP, one item per segment) or in warp items of 32, 64
  * or 128 splits (the tile).  mt4g_autotune times mt4g_ks_scan with each choice on up to 256
  * series of every (floor log2 T, floor log2 m) bucket present in the batch (copied into a
- * temporary buffer) and keeps the fastest per bucket in the context; later calls use it for
+ * temporary buffer) and keeps the fastest per bucket in the context; the run sweep is a
+ * candidate only where it takes at least half of the bucket's series (the others would run as
+ * slices inside the sweep kernel, which holds fewer warps).  Later calls use the table for
  * series of that bucket (default: the run sweep).  Synchronises the stream.  The table can be
  * written to and read from a text file; mt4g_autotune_get returns the choice (1, 2 or 4
  * groups of 32, or MT4G_SCAN_SWEEP) used for a shape.

@@ -1721,7 +1721,11 @@ extern "C" int mt4g_autotune(mt4g_ctx *ctx, const uint32_t *samples, const int64
                 if (rep == 1 || (rep > 1 && t < ms)) ms = t;
             }
             if (rc) break;
-            if (ms < best_ms) {
+            // the run sweep counts for a bucket only if it takes most of its series (at most 1536
+            // distinct values): the others would run as slices inside the sweep kernel, which
+            // holds half the warps of the slice kernel, and a whole batch would pay for that
+            const bool usable = kpt != MT4G_SCAN_SWEEP || 2 * (int64_t)ctx->h_hdr->unswept <= n;
+            if (usable && ms < best_ms) {
                 best_ms = ms;
                 best = kpt;
             }

@@ -824,9 +824,6 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
     // run indices two steps ahead (global loads in flight over two splits); the layout
     // positions of step k's samples are looked up at the top of split k and used by its moves
     // at the end, so the lookups' latency is spent under the evaluation
-    StepBuf<VEC> nxt, nxt2;
-    sweep_load_step<VEC>(rk, A, m, lane, nxt);
-    if (A + 1 <= B) sweep_load_step<VEC>(rk, A + 1, m, lane, nxt2);
     bk = kNoK;
     bg = 0;
     uint32_t gk = 0;  // g of split kb + lane
@@ -861,107 +858,129 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
             kb = kp + 1;
         }
     };
-    // with skipping the best is kept current (the same on every lane)
-    int e = -1;       // last evaluated split
-    uint64_t ge = 0;  // its g
-    bool pev = false;  // split k - 1 was evaluated
-    nev = 0;
-    auto finish_now = [&](int kp) {
-        const uint32_t g = split_g();
-        if (better(kp, (uint64_t)g, bk, bg, lo, hi)) {
-            bk = kp;
-            bg = g;
-        }
-        e = kp;
-        ge = g;
-    };
     const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
-    for (int k = A; k <= B; k++) {
-        const StepBuf<VEC> cur = nxt;
-        uint32_t pos0 = 0, pos1 = 0, pos2 = 0, pos3 = 0;
-        if (VEC && 4 * lane < m) {
-            pos0 = ss.map[cur.v[0] & 0xffffu];
-            pos1 = ss.map[cur.v[0] >> 16];
-            pos2 = ss.map[cur.v[1] & 0xffffu];
-            pos3 = ss.map[cur.v[1] >> 16];
-        }
-        nxt = nxt2;
-        if (k + 2 <= B) sweep_load_step<VEC>(rk, k + 2, m, lane, nxt2);
-        __syncwarp();
-        // the first group of the block (two quads, 8 runs) while split k - 1 is finished
+    // the values of split k into p_blk, p_h0, p_mx, p_mn (l holds the left counts of split k)
+    auto evaluate = [&](int k) {
+        const uint32_t a = (uint32_t)(k - lo), na = 0u - a;
+        const uint32_t h0 = a * Cb;
+        uint32_t hc = h0;
+        int32_t mx = INT_MIN, mn = INT_MAX;
         uint4 q0 = lq[0], q1 = zero4;
         if (nq > 1) q1 = lq[1];
-        bool ev = true;  // split k is evaluated (the same on every lane)
-        if constexpr (SKIP) {
-            if (pev) finish_now(k - 1);
-            if (e >= 0) {
-                const uint64_t ub = ge + (uint64_t)(k - e) * (uint64_t)m * (uint64_t)H;
-                const uint64_t db = (uint64_t)(bk - lo) * (uint64_t)(hi - bk);
-                const uint64_t dk = (uint64_t)(k - lo) * (uint64_t)(hi - k);
-                ev = !prod_less(ub, db, bg, dk);
-            }
-            pev = ev;
-        } else {
-            if (k > A) finish(k - 1);
-        }
-        if (ev) {
-            nev++;
-            const uint32_t a = (uint32_t)(k - lo), na = 0u - a;
-            const uint32_t h0 = a * Cb;
-            uint32_t hc = h0;
-            int32_t mx = INT_MIN, mn = INT_MAX;
-            // the block in groups of two quads, the next group's loads issued before the
-            // current group is evaluated; nq is the same for every lane
+        // the block in groups of two quads, the next group's loads issued before the current
+        // group is evaluated; nq is the same for every lane
 #pragma unroll
-            for (int g = 0; g < kSweepMaxR / 8; g++) {
-                if (2 * g >= nq) break;
-                uint4 n0 = zero4, n1 = zero4;
-                if (2 * g + 2 < nq) n0 = lq[2 * g + 2];
-                if (2 * g + 3 < nq) n1 = lq[2 * g + 3];
-                sweep_eval4(q0, Cr[8 * g], Cr[8 * g + 1], Cr[8 * g + 2], Cr[8 * g + 3], na, hc, mx, mn);
-                if (2 * g + 1 < nq)
-                    sweep_eval4(q1, Cr[8 * g + 4], Cr[8 * g + 5], Cr[8 * g + 6], Cr[8 * g + 7], na, hc, mx, mn);
-                q0 = n0;
-                q1 = n1;
-            }
-            p_blk = hc - h0;  // sum of l over the block
-            p_h0 = h0;
-            p_mx = mx;
-            p_mn = mn;
+        for (int g = 0; g < kSweepMaxR / 8; g++) {
+            if (2 * g >= nq) break;
+            uint4 n0 = zero4, n1 = zero4;
+            if (2 * g + 2 < nq) n0 = lq[2 * g + 2];
+            if (2 * g + 3 < nq) n1 = lq[2 * g + 3];
+            sweep_eval4(q0, Cr[8 * g], Cr[8 * g + 1], Cr[8 * g + 2], Cr[8 * g + 3], na, hc, mx, mn);
+            if (2 * g + 1 < nq)
+                sweep_eval4(q1, Cr[8 * g + 4], Cr[8 * g + 5], Cr[8 * g + 6], Cr[8 * g + 7], na, hc, mx, mn);
+            q0 = n0;
+            q1 = n1;
         }
-        // every lane has read l for split k: step k's samples move left now (reductions the warp
-        // does not wait for)
-        __syncwarp();
-        if (k < B) {
-            if constexpr (VEC) {
-                if (4 * lane < m) {
-                    atomicAdd(&ss.l[pos0], H);
-                    atomicAdd(&ss.l[pos1], H);
-                    atomicAdd(&ss.l[pos2], H);
-                    atomicAdd(&ss.l[pos3], H);
-                }
-                const uint16_t *src = rk + (int64_t)k * m;
-                for (int j0 = 128; j0 < m; j0 += 128) {
-                    const bool a2 = j0 + 4 * lane < m;
-                    uint2 x = make_uint2(0u, 0u);
-                    if (a2) x = __ldg(reinterpret_cast<const uint2 *>(src + j0) + lane);
-                    lc_add(ss, x.x & 0xffffu, H, a2);
-                    lc_add(ss, x.x >> 16, H, a2);
-                    lc_add(ss, x.y & 0xffffu, H, a2);
-                    lc_add(ss, x.y >> 16, H, a2);
-                }
-            } else {
-                sweep_apply_step<VEC>(ss, rk, k, m, H, lane, cur);
-            }
-        }
-    }
+        p_blk = hc - h0;  // sum of l over the block
+        p_h0 = h0;
+        p_mx = mx;
+        p_mn = mn;
+    };
+    nev = 0;
     if constexpr (SKIP) {
-        if (pev) finish_now(B);
+        // Walk: evaluate split k; the bound from it, with the best so far, excludes a run of the
+        // following splits (lane i tests split k + 1 + i, a ballot gives the run's length); the
+        // steps up to the next split to evaluate move left in one pass, with no per-split work.
+        int k = A;
+        StepBuf<VEC> cur;
+        sweep_load_step<VEC>(rk, A, m, lane, cur);
+        while (k <= B) {
+            __syncwarp();
+            evaluate(k);
+            const uint32_t g = split_g();
+            nev++;
+            if (better(k, (uint64_t)g, bk, bg, lo, hi)) {
+                bk = k;
+                bg = g;
+            }
+            const uint64_t db = (uint64_t)(bk - lo) * (uint64_t)(hi - bk);
+            int next = k + 1;
+            for (;;) {
+                const int kk = next + lane;
+                bool skip = false;
+                if (kk <= B) {
+                    const uint64_t ub = (uint64_t)g + (uint64_t)(kk - k) * (uint64_t)m * (uint64_t)H;
+                    const uint64_t dk = (uint64_t)(kk - lo) * (uint64_t)(hi - kk);
+                    skip = prod_less(ub, db, bg, dk);
+                }
+                const unsigned sm = __ballot_sync(kFull, skip);
+                const int run = sm == kFull ? 32 : __ffs(~sm) - 1;
+                next += run;
+                if (run < 32) break;
+            }
+            if (next > B) break;  // every remaining split is excluded
+            // every lane has read l for split k: steps k .. next - 1 move left
+            __syncwarp();
+            sweep_apply_step<VEC>(ss, rk, k, m, H, lane, cur);  // step k, loaded during split k
+            for (int t = k + 1; t < next; t++) {
+                StepBuf<VEC> b;
+                sweep_load_step<VEC>(rk, t, m, lane, b);
+                sweep_apply_step<VEC>(ss, rk, t, m, H, lane, b);
+            }
+            k = next;
+            if (k <= B) sweep_load_step<VEC>(rk, k, m, lane, cur);
+        }
+        __syncwarp();
+        return;
     } else {
+        StepBuf<VEC> nxt, nxt2;
+        sweep_load_step<VEC>(rk, A, m, lane, nxt);
+        if (A + 1 <= B) sweep_load_step<VEC>(rk, A + 1, m, lane, nxt2);
+        for (int k = A; k <= B; k++) {
+            const StepBuf<VEC> cur = nxt;
+            uint32_t pos0 = 0, pos1 = 0, pos2 = 0, pos3 = 0;
+            if (VEC && 4 * lane < m) {
+                pos0 = ss.map[cur.v[0] & 0xffffu];
+                pos1 = ss.map[cur.v[0] >> 16];
+                pos2 = ss.map[cur.v[1] & 0xffffu];
+                pos3 = ss.map[cur.v[1] >> 16];
+            }
+            nxt = nxt2;
+            if (k + 2 <= B) sweep_load_step<VEC>(rk, k + 2, m, lane, nxt2);
+            __syncwarp();
+            if (k > A) finish(k - 1);
+            nev++;
+            evaluate(k);
+            // every lane has read l for split k: step k's samples move left now (reductions the warp
+            // does not wait for)
+            __syncwarp();
+            if (k < B) {
+                if constexpr (VEC) {
+                    if (4 * lane < m) {
+                        atomicAdd(&ss.l[pos0], H);
+                        atomicAdd(&ss.l[pos1], H);
+                        atomicAdd(&ss.l[pos2], H);
+                        atomicAdd(&ss.l[pos3], H);
+                    }
+                    const uint16_t *src = rk + (int64_t)k * m;
+                    for (int j0 = 128; j0 < m; j0 += 128) {
+                        const bool a2 = j0 + 4 * lane < m;
+                        uint2 x = make_uint2(0u, 0u);
+                        if (a2) x = __ldg(reinterpret_cast<const uint2 *>(src + j0) + lane);
+                        lc_add(ss, x.x & 0xffffu, H, a2);
+                        lc_add(ss, x.x >> 16, H, a2);
+                        lc_add(ss, x.y & 0xffffu, H, a2);
+                        lc_add(ss, x.y >> 16, H, a2);
+                    }
+                } else {
+                    sweep_apply_step<VEC>(ss, rk, k, m, H, lane, cur);
+                }
+            }
+        }
         finish(B);
         warp_best(bk, bg, lo, hi);
+        __syncwarp();
     }
-    __syncwarp();
 }
 
 // Reserve `tot` queue slots and count them as pending (one lane).  Returns the first slot,

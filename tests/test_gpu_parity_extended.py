@@ -240,3 +240,45 @@ def test_sweep_bound_skipping_learned_mode(eng):
         _check_segment(eng, b, 1e-6, mode=mt4g.MODE_LEARNED)
     finally:
         eng.set_option(mt4g.OPT_SWEEP_SKIP, 0)
+
+
+def test_many_distinct_values_match_oracle(eng):
+    """Series with 1.6k to 9.7k distinct values (beyond the run sweep's 1536: scanned in slices
+    whatever tile is asked for), three value levels each, a series with more than 11552 values
+    and one with m not a multiple of 4: every answer equals the oracle's, with the default plan and
+    with the run sweep forced (its series go back to the queue as slices)."""
+    rng = np.random.default_rng(83)
+    series = []
+    for U in (1700, 2600, 5000, 9000, 11000):
+        m = int(rng.choice([4, 8, 12]))
+        T = min(4000, max(120, -(-5 * U // m)))  # about five samples per value
+        cps = np.sort(rng.choice(np.arange(T // 5, 4 * T // 5), size=2, replace=False))
+        level = np.searchsorted(cps, np.arange(T), side="right")  # 0, 1, 2: three value ranges
+        x = rng.integers(0, U // 3, size=(T, m)) + (level * (U // 3))[:, None]
+        series.append(x.astype(np.uint32))
+    x = rng.integers(0, 40000, size=(200, 100)).astype(np.uint32)  # beyond 11552 distinct values
+    x[90:] += 20000
+    series.append(x)
+    x = rng.integers(0, 3000, size=(300, 10)).astype(np.uint32)  # m = 10: no 8-byte rows
+    x[150:] += 900
+    series.append(x)
+    b = synth.from_arrays(series)
+    U_all = [len(np.unique(b.series(s))) for s in range(b.S)]
+    assert min(U_all[:5]) > 1536 and U_all[5] > 11552
+    d = mt4g.to_device_samples(b.samples)
+    oseg = oracle.ks_segment(b.samples, b.offsets, b.steps, 1e-6, 1, 16, nthreads=8)[1:]
+    oscan = oracle.ks_scan(b.samples, b.offsets, b.steps, nthreads=8)
+    try:
+        for kpt in (0, mt4g.SCAN_SWEEP):
+            eng.set_option(mt4g.OPT_SCAN_KPT, kpt)
+            r = eng.ks_segment(d, b.offsets, b.steps, 1e-6, 1, 16)
+            got = [t.cpu().numpy() for t in r[1:6]]
+            for a, c in zip(got[:4], oseg[:4]):
+                assert np.array_equal(a, c), kpt
+            assert _close(got[4], oseg[4], P_RTOL)
+            sc = [t.cpu().numpy() for t in eng.ks_scan(d, b.offsets, b.steps)]
+            for a, c in zip(sc[:3], oscan[:3]):
+                assert np.array_equal(a, c), kpt
+            assert _close(sc[3], oscan[3], P_RTOL)
+    finally:
+        eng.set_option(mt4g.OPT_SCAN_KPT, 0)

@@ -153,3 +153,4 @@ def test_counting_sort_tables():
         for q in (N // 2, (50 * N + 99) // 100 - 1, (95 * N + 99) // 100 - 1):
             r = int(np.searchsorted(rt, q, side="right") - 1)
             assert x.min() + present[r] == s[q]
+
