@@ -50,7 +50,7 @@ WORKLOADS = {
     "plain": (2, 1, 1024, False, "plain full segmentation, 1024 series x T=512 x m=128 uint32"),
     "uneven": (3, 2, 16384, False, "plain full segmentation, 16384 uneven series, T 32..4096, m 8..256"),
 }
-LAUNCHES = {False: 4, True: 14}  # our kernels per call (plain / learned)
+LAUNCHES = {False: 4, True: 8}  # our kernels per call (plain / learned)
 RECIPES = {2: "synth recipe 2 (T=512, m=128, levels 35/300/800/1100, 0.5% outliers)",
            3: "synth recipe 3 (T 32..4096, m 8..256, 0-4 level ratios 1.01..30, Pareto tails)"}
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch, per series, from the ncu
@@ -291,6 +291,23 @@ def main():
         line["cuda_graph"] = True
         line["autotune"] = {"seconds": tune_s, "tiles": dict(sorted(tiles.items())),
                             "tile_codes": "1/2/4 = groups of 32 splits per work item, 8 = run sweep"}
+        # the learned path on the same batch (the network trained on the three-level recipe; its
+        # window and grid probes serve the series scanned in slices), direct calls with the same
+        # tiles, answers compared with the plain call's on the device
+        eng.cnn_load(WEIGHTS)
+        res_p = [x.clone() for x in out_main[1:6]]
+        graph = False
+        t_l, out_l, _, stages_l, evals_l, _ = timed(mt4g.MODE_LEARNED, args.steps, 1)
+        st_l = eng.learned_stats()
+        same_l = torch.ones(S, dtype=torch.bool, device=dev)
+        for a_, c_ in zip(res_p, out_l[1:6]):
+            same_l &= (a_ == c_).reshape(S, -1).all(dim=1)
+        line["learned"] = {"value": S * world * args.steps / t_l, "ms_per_step": t_l / args.steps * 1e3,
+                           "speedup_vs_plain": t_main / t_l, "agreement": float(same_l.float().mean().item()),
+                           "fallback_rate": float(out_l[6].float().mean().item()), "evals": evals_l,
+                           "evals_plain": evals, "certified_segments": st_l["certified"],
+                           "refined_segments": st_l["refined"],
+                           "stage_ms": dict(zip(STAGES, np.asarray(stages_l).mean(axis=0).tolist()))}
     if learned:
         res_l = [x.clone() for x in out_main[1:6]]
         fb = out_main[6].clone()

@@ -1130,7 +1130,9 @@ struct CnnBuffers {
     CnnActs A;
     uint16_t *feat;
     SeriesDesc *desc;
-    int64_t *tiles_before;
+    int64_t *tiles_before;  // tiles of 128 positions (training passes)
+    int64_t *infer_before;  // tiles of the one-kernel inference
+    int64_t ninfer;
     int32_t *win;
     float *conf;
 };
@@ -1138,17 +1140,19 @@ struct CnnBuffers {
 // Layout of the proposal workspace for `rows` padded rows and S series.
 size_t carve_cnn(void *base, int64_t rows, int64_t S, bool training, bool own_feat, int32_t n_win, CnnBuffers &B) {
     Carver c(base);
-    B.A.a1 = c.take<uint16_t>(rows * 32);
-    B.A.a2 = c.take<uint16_t>(rows * 32);
-    B.A.a3 = c.take<uint16_t>(rows * 32);
+    // hidden activations in memory only for the backward pass; inference keeps them on chip
+    B.A.a1 = c.take<uint16_t>(training ? rows * 32 : 0);
+    B.A.a2 = c.take<uint16_t>(training ? rows * 32 : 0);
+    B.A.a3 = c.take<uint16_t>(training ? rows * 32 : 0);
     B.A.logits = c.take<float>(rows);
     B.A.g = c.take<float>(training ? rows : 0);
     B.A.dz1 = c.take<float>(training ? rows * 32 : 0);
     B.A.dz2 = c.take<float>(training ? rows * 32 : 0);
     B.A.dz3 = c.take<float>(training ? rows * 32 : 0);
     B.A.inv_valid = c.take<float>(16);
-    B.tiles_before = c.take<int64_t>(S);
+    B.tiles_before = c.take<int64_t>(2 * S);  // the two tile prefixes, uploaded together
     B.A.tiles_before = B.tiles_before;
+    B.infer_before = B.tiles_before ? B.tiles_before + S : nullptr;
     B.desc = c.take<SeriesDesc>(S);
     B.feat = c.take<uint16_t>(own_feat ? rows * kFeatC : 0);
     B.win = c.take<int32_t>(own_feat ? S * n_win : 0);
@@ -1184,33 +1188,34 @@ int ensure_cnn_ws(mt4g_ctx *c, size_t bytes) {
 // Host tables of a feature batch: descriptors (step bases) and tile prefixes.
 int upload_cnn_tables(mt4g_ctx *c, const std::vector<SeriesDesc> &desc, CnnBuffers &B, int64_t *ntiles,
                       cudaStream_t st) {
-    std::vector<int64_t> tb;
+    std::vector<int64_t> tb, ib;
     *ntiles = cnn_tiles(desc, tb);
+    B.ninfer = cnn_infer_tiles(desc, ib);
     const size_t S = desc.size();
     int rc = MT4G_OK;
-    char *h = (char *)stage_alloc(c, S * (sizeof(SeriesDesc) + sizeof(int64_t)) + 64, &rc);
+    char *h = (char *)stage_alloc(c, S * (sizeof(SeriesDesc) + 2 * sizeof(int64_t)) + 64, &rc);
     if (rc) return rc;
     memcpy(h, desc.data(), S * sizeof(SeriesDesc));
     memcpy(h + S * sizeof(SeriesDesc), tb.data(), S * sizeof(int64_t));
+    memcpy(h + S * (sizeof(SeriesDesc) + sizeof(int64_t)), ib.data(), S * sizeof(int64_t));
     const cudaStream_t us = upload_stream(c, st);
     CUDA_TRY(c, cudaMemcpyAsync(B.desc, h, S * sizeof(SeriesDesc), cudaMemcpyHostToDevice, us));
-    CUDA_TRY(c, cudaMemcpyAsync(B.tiles_before, h + S * sizeof(SeriesDesc), S * sizeof(int64_t),
+    CUDA_TRY(c, cudaMemcpyAsync(B.tiles_before, h + S * sizeof(SeriesDesc), 2 * S * sizeof(int64_t),
                                 cudaMemcpyHostToDevice, us));
     CUDA_TRY(c, staged(c, us));
     CUDA_TRY(c, uploads_done(c, us, st));
     return MT4G_OK;
 }
 
-int zero_pads(mt4g_ctx *c, CnnBuffers &B, int64_t S, bool training, cudaStream_t st) {
+// Zero pad rows of the training pass's activation and gradient arrays.
+int zero_pads(mt4g_ctx *c, CnnBuffers &B, int64_t S, cudaStream_t st) {
     CUDA_TRY(c, launch_zero_pad_rows(B.A.a1, 64, B.desc, S, st));
     CUDA_TRY(c, launch_zero_pad_rows(B.A.a2, 64, B.desc, S, st));
     CUDA_TRY(c, launch_zero_pad_rows(B.A.a3, 64, B.desc, S, st));
-    if (training) {
-        CUDA_TRY(c, launch_zero_pad_rows(B.A.g, 4, B.desc, S, st));
-        CUDA_TRY(c, launch_zero_pad_rows(B.A.dz1, 128, B.desc, S, st));
-        CUDA_TRY(c, launch_zero_pad_rows(B.A.dz2, 128, B.desc, S, st));
-        CUDA_TRY(c, launch_zero_pad_rows(B.A.dz3, 128, B.desc, S, st));
-    }
+    CUDA_TRY(c, launch_zero_pad_rows(B.A.g, 4, B.desc, S, st));
+    CUDA_TRY(c, launch_zero_pad_rows(B.A.dz1, 128, B.desc, S, st));
+    CUDA_TRY(c, launch_zero_pad_rows(B.A.dz2, 128, B.desc, S, st));
+    CUDA_TRY(c, launch_zero_pad_rows(B.A.dz3, 128, B.desc, S, st));
     return MT4G_OK;
 }
 
@@ -1438,10 +1443,9 @@ int mt4g_cnn_forward(mt4g_ctx *c, const uint16_t *feat, const int32_t *steps, in
     int64_t ntiles = 0;
     rc = upload_cnn_tables(c, desc, B, &ntiles, st);
     if (rc) return rc;
-    rc = zero_pads(c, B, S, false, st);
-    if (rc) return rc;
     CUDA_TRY(c, cnn_prepare(c->cnn, st));
-    CUDA_TRY(c, cnn_forward(c->cnn, feat, B.A, B.desc, B.tiles_before, S, ntiles, c->wait_limit_ns, nullptr, st));
+    CUDA_TRY(c, cnn_infer(c->cnn, feat, logits_out, B.desc, B.infer_before, S, B.ninfer, c->wait_limit_ns, nullptr,
+                          st));
     c->last_stream = st;
     c->have_last = true;
     return MT4G_OK;
@@ -1465,7 +1469,7 @@ static int cnn_fwd_bwd(mt4g_ctx *c, const uint16_t *feat, int32_t T, int64_t Bn,
     int64_t ntiles = 0;
     rc = upload_cnn_tables(c, desc, B, &ntiles, st);
     if (rc) return rc;
-    rc = zero_pads(c, B, Bn, true, st);
+    rc = zero_pads(c, B, Bn, st);
     if (rc) return rc;
     CUDA_TRY(c, cnn_prepare(c->cnn, st));
     CUDA_TRY(c, cnn_forward(c->cnn, feat, B.A, B.desc, B.tiles_before, Bn, ntiles, c->wait_limit_ns, nullptr, st));
@@ -1528,12 +1532,10 @@ int mt4g_propose(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets,
     int64_t ntiles = 0;
     rc = upload_cnn_tables(ctx, P.desc, C, &ntiles, st);
     if (rc) return rc;
-    rc = zero_pads(ctx, C, S, false, st);
-    if (rc) return rc;
     CUDA_TRY(ctx, launch_summaries(samples, B.desc, S, C.feat, st));
     CUDA_TRY(ctx, cnn_prepare(ctx->cnn, st));
-    CUDA_TRY(ctx, cnn_forward(ctx->cnn, C.feat, C.A, B.desc, C.tiles_before, S, ntiles, ctx->wait_limit_ns,
-                              &B.q->status, st));
+    CUDA_TRY(ctx, cnn_infer(ctx->cnn, C.feat, C.A.logits, B.desc, C.infer_before, S, C.ninfer, ctx->wait_limit_ns,
+                            &B.q->status, st));
     CUDA_TRY(ctx, launch_propose(C.A.logits, B.desc, S, n_win, half_width, win_center, conf, st));
     mark(ctx, 3, st);
     mark(ctx, 4, st);
@@ -1562,15 +1564,13 @@ int enqueue_proposals(mt4g_ctx *ctx, const uint32_t *samples, Plan &P, Buffers &
     int64_t ntiles = 0;
     rc = upload_cnn_tables(ctx, P.desc, C, &ntiles, st);
     if (rc) return rc;
-    rc = zero_pads(ctx, C, S, false, st);
-    if (rc) return rc;
     // in sweep calls the sort counted the series the sweep does not take: only they use the
     // proposals, and with none the proposal kernels return at once
     const unsigned long long *gate = P.use_sweep ? &B.q->unswept : nullptr;
     CUDA_TRY(ctx, launch_summaries(samples, B.desc, S, C.feat, st, gate));
     CUDA_TRY(ctx, cnn_prepare(ctx->cnn, st));
-    CUDA_TRY(ctx, cnn_forward(ctx->cnn, C.feat, C.A, B.desc, C.tiles_before, S, ntiles, ctx->wait_limit_ns,
-                              &B.q->status, st, gate));
+    CUDA_TRY(ctx, cnn_infer(ctx->cnn, C.feat, C.A.logits, B.desc, C.infer_before, S, C.ninfer, ctx->wait_limit_ns,
+                            &B.q->status, st, gate));
     CUDA_TRY(ctx, launch_propose(C.A.logits, B.desc, S, ctx->n_win, ctx->half, C.win, C.conf, st, gate));
     R.win_center = C.win;
     R.n_win = ctx->n_win;

@@ -57,6 +57,13 @@ cudaError_t cnn_hidden_tc(int layer, const __nv_bfloat16 *in, const float *W, co
                           const SeriesDesc *desc, const int64_t *tiles_before, int64_t S, int64_t ntiles,
                           long long wait_limit_ns, int32_t *status, cudaStream_t st,
                           const unsigned long long *gate = nullptr);
+// Inference in one kernel (conv_tc.cu): logits of every step of every series, written at the
+// feature rows of the steps (pad rows untouched).  Tiles of 116 positions; tiles_before is the
+// prefix of cnn_infer_tiles.
+int64_t cnn_infer_tiles(const std::vector<SeriesDesc> &desc, std::vector<int64_t> &tiles_before);
+cudaError_t cnn_infer(const CnnState &W, const uint16_t *feat, float *logits, const SeriesDesc *desc,
+                      const int64_t *tiles_before, int64_t S, int64_t ntiles, long long wait_limit_ns, int32_t *status,
+                      cudaStream_t st, const unsigned long long *gate = nullptr);
 cudaError_t cnn_backward(const CnnState &W, const uint16_t *feat, const CnnActs &A, const int32_t *cp_count,
                          const int32_t *cp_idx, int32_t max_cp, const SeriesDesc *desc, int64_t S, int T,
                          float *grad, float *loss, cudaStream_t st);

@@ -10,9 +10,13 @@
 // Values are read as at least 1.  Features are computed in FP32 and stored as BF16
 // (round to nearest even) in rows of kFeatC channels (the last is zero).
 //
-// One warp per step: the step's m <= 256 samples are sorted in registers by a bitonic
-// network (V values per lane, partners across lanes by shuffle), then lanes 0..15 pick
-// their quantile.  Each warp takes every eighth step and loads the next one while sorting.
+// Steps of m = 32, 64 or 128 samples: one thread per step.  A warp copies 32 consecutive
+// steps into a padded shared-memory stage (cp.async), each thread reads its step's row into
+// registers, the warp starts copying its next 32 steps, and each thread sorts its row with
+// Batcher's odd-even merge network on compile-time register indices (no shuffles; the
+// compiler drops the exchanges that no selected rank depends on).  Other m <= 256: one warp
+// per step, a bitonic network with V values per lane and partners across lanes by shuffle,
+// then lanes 0..15 pick their quantile; each warp loads its next step while sorting.
 #include <cuda_bf16.h>
 
 #include "mt4g_internal.cuh"
@@ -22,6 +26,110 @@ namespace mt4g {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kSumWarps = 4;  // warps per block (one block per series)
+constexpr int kRowMax = 128;  // largest m sorted one step per thread
+// stage of one warp: 32 rows of m words at a stride of m + 4 words (16-byte aligned rows; the
+// eight lanes of a quarter warp start their 16-byte reads in eight different bank groups)
+constexpr int kStageWords = 32 * (kRowMax + 4);
+constexpr size_t kSumSmem = (size_t)kSumWarps * kStageWords * sizeof(uint32_t);
+
+__device__ __forceinline__ void cmpx(uint32_t &a, uint32_t &b) {
+    const uint32_t lo = min(a, b), hi = max(a, b);
+    a = lo;
+    b = hi;
+}
+
+// Batcher's odd-even merge of x[LO, LO + LEN), whose halves are sorted, comparing elements R
+// apart: merge the even and the odd subsequences (stride 2R), then exchange neighbours.
+template <int LO, int LEN, int R, int N>
+__device__ __forceinline__ void oe_merge(uint32_t (&x)[N]) {
+    if constexpr (2 * R < LEN) {
+        oe_merge<LO, LEN, 2 * R>(x);
+        oe_merge<LO + R, LEN, 2 * R>(x);
+#pragma unroll
+        for (int i = LO + R; i + R < LO + LEN; i += 2 * R) cmpx(x[i], x[i + R]);
+    } else {
+        cmpx(x[LO], x[LO + R]);
+    }
+}
+
+template <int LO, int LEN, int N>
+__device__ __forceinline__ void oe_sort(uint32_t (&x)[N]) {
+    if constexpr (LEN > 1) {
+        oe_sort<LO, LEN / 2>(x);
+        oe_sort<LO + LEN / 2, LEN / 2>(x);
+        oe_merge<LO, LEN, 1>(x);
+    }
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ uint32_t bf16_pair(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+// Features of the steps of one series with m == N, one thread per step: groups of 32 steps
+// warp, warp + kSumWarps, ...; the next group is copied into the stage while this one sorts.
+template <int N>
+__device__ void summarise_rows(const uint32_t *__restrict__ x0, int T, float lmed, int warp, uint32_t *stage,
+                               __nv_bfloat16 *__restrict__ base) {
+    static_assert(N % 4 == 0 && N <= kRowMax, "row size");
+    constexpr int RS = N + 4;  // row stride in words
+    const int lane = threadIdx.x & 31;
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(stage);
+    const bool vec = (reinterpret_cast<uintptr_t>(x0) & 15) == 0;  // rows of N words stay aligned
+    auto issue = [&](int g) {
+        const int t0 = g * 32, rows = min(32, T - t0);
+        const uint32_t *src = x0 + (int64_t)t0 * N;
+        if (vec) {
+            constexpr int Q = N / 4;
+            for (int p = lane; p < rows * Q; p += 32)
+                cp_async16(sbase + (uint32_t)((p / Q) * RS + (p % Q) * 4) * 4u, src + (int64_t)p * 4);
+        } else {
+            for (int p = lane; p < rows * N; p += 32)
+                cp_async4(sbase + (uint32_t)((p / N) * RS + p % N) * 4u, src + p);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    if (warp * 32 < T) issue(warp);
+    for (int g = warp; g * 32 < T; g += kSumWarps) {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncwarp();
+        uint32_t x[N];
+        const uint4 *row = reinterpret_cast<const uint4 *>(stage + lane * RS);
+#pragma unroll
+        for (int q = 0; q < N / 4; q++) {
+            const uint4 v = row[q];
+            x[4 * q] = v.x;
+            x[4 * q + 1] = v.y;
+            x[4 * q + 2] = v.z;
+            x[4 * q + 3] = v.w;
+        }
+        __syncwarp();
+        if ((g + kSumWarps) * 32 < T) issue(g + kSumWarps);
+        oe_sort<0, N>(x);
+        const int t = g * 32 + lane;
+        if (t < T) {
+            float f[kFeatC];
+#pragma unroll
+            for (int i = 0; i < 16; i++) {
+                const int rank = ((2 * i + 1) * N) / 32 < N - 1 ? ((2 * i + 1) * N) / 32 : N - 1;
+                f[i] = log2f((float)max(x[rank], 1u)) - lmed;
+            }
+            f[16] = log2f(1024.f + 32.f * (float)t) - 10.f;
+            f[17] = 0.f;
+            uint32_t *dst = reinterpret_cast<uint32_t *>(base + (int64_t)(2 + t) * kFeatC);
+#pragma unroll
+            for (int j = 0; j < kFeatC / 2; j++) dst[j] = bf16_pair(f[2 * j], f[2 * j + 1]);
+        }
+    }
+}
 
 // Ascending bitonic sort of 32 V values; lane l holds elements l V .. l V + V - 1.  The
 // direction of a compare-exchange depends on the element's index only through bits >= log2 V
@@ -60,8 +168,8 @@ __device__ __forceinline__ void bitonic_sort_warp(uint32_t (&x)[V]) {
     }
 }
 
-// Features of steps warp, warp + 8, ... of one series; each step's samples are loaded one
-// step ahead, so the loads of the next step are in flight while this one is sorted.
+// Features of steps warp, warp + kSumWarps, ... of one series; each step's samples are
+// loaded one step ahead, so the loads of the next step are in flight while this one is sorted.
 template <int V>
 __device__ void summarise_steps(const uint32_t *__restrict__ x0, int T, int m, float lmed, int warp,
                                 __nv_bfloat16 *__restrict__ base) {
@@ -78,11 +186,11 @@ __device__ void summarise_steps(const uint32_t *__restrict__ x0, int T, int m, f
     if (warp < T) load(warp, nx);
     const int i = lane & 15;
     const int rank = min(m - 1, ((2 * i + 1) * m) / 32);
-    for (int t = warp; t < T; t += 8) {
+    for (int t = warp; t < T; t += kSumWarps) {
         uint32_t x[V];
 #pragma unroll
         for (int r = 0; r < V; r++) x[r] = nx[r];
-        if (t + 8 < T) load(t + 8, nx);
+        if (t + kSumWarps < T) load(t + kSumWarps, nx);
         bitonic_sort_warp<V>(x);
         uint32_t q = 0;
 #pragma unroll
@@ -99,7 +207,7 @@ __device__ void summarise_steps(const uint32_t *__restrict__ x0, int T, int m, f
     }
 }
 
-__global__ void __launch_bounds__(256, 4) summaries_kernel(const uint32_t *__restrict__ samples,
+__global__ void __launch_bounds__(kSumWarps * 32, 3) summaries_kernel(const uint32_t *__restrict__ samples,
                                                         const SeriesDesc *__restrict__ desc,
                                                         __nv_bfloat16 *__restrict__ feat,
                                                         const unsigned long long *__restrict__ gate) {
@@ -117,7 +225,15 @@ __global__ void __launch_bounds__(256, 4) summaries_kernel(const uint32_t *__res
         }
     }
     const uint32_t *x0 = samples + d.off;
-    if (d.m <= 32)
+    extern __shared__ __align__(16) uint32_t sum_stage[];
+    uint32_t *stage = sum_stage + warp * kStageWords;
+    if (d.m == 128)
+        summarise_rows<128>(x0, d.T, lmed, warp, stage, base);
+    else if (d.m == 64)
+        summarise_rows<64>(x0, d.T, lmed, warp, stage, base);
+    else if (d.m == 32)
+        summarise_rows<32>(x0, d.T, lmed, warp, stage, base);
+    else if (d.m <= 32)
         summarise_steps<1>(x0, d.T, d.m, lmed, warp, base);
     else if (d.m <= 64)
         summarise_steps<2>(x0, d.T, d.m, lmed, warp, base);
@@ -132,7 +248,17 @@ __global__ void __launch_bounds__(256, 4) summaries_kernel(const uint32_t *__res
 cudaError_t launch_summaries(const uint32_t *samples, const SeriesDesc *raw_desc, int64_t S, uint16_t *feat,
                              cudaStream_t st, const unsigned long long *gate) {
     if (S <= 0) return cudaSuccess;
-    summaries_kernel<<<(unsigned)S, 256, 0, st>>>(samples, raw_desc, reinterpret_cast<__nv_bfloat16 *>(feat), gate);
+    static int configured_device = -1;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (configured_device != dev) {
+        e = cudaFuncSetAttribute(summaries_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSumSmem);
+        if (e != cudaSuccess) return e;
+        configured_device = dev;
+    }
+    summaries_kernel<<<(unsigned)S, kSumWarps * 32, kSumSmem, st>>>(samples, raw_desc,
+                                                                   reinterpret_cast<__nv_bfloat16 *>(feat), gate);
     return cudaGetLastError();
 }
 
