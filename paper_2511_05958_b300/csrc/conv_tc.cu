@@ -264,23 +264,26 @@ cudaError_t launch_one(const __nv_bfloat16 *in, const float *W, const float *bia
 // and the last layer (32 -> 1, on CUDA cores) gives the kFzOut = 116 logits of positions
 // P + 8 .. P + 123; consecutive tiles of a series start 116 positions apart (P = -8, 108, ...).
 // Activations stay in shared memory; rows at positions outside [0, T) are zero at every layer,
-// which is the zero padding of each convolution.
+// which is the zero padding of each convolution.  Four CTAs of 48 KB share an SM, each with one
+// tile in flight; the next tile's input is copied while layers 2 and 3 run.
 //
 // Operand layout: each buffer stores, for every 8-channel chunk kc, a column of rows 16 bytes
 // apart (row r of chunk kc at kc * kFzLbo + 16 r).  This is the K-major no-swizzle canonical
 // layout with 8-row core matrices 128 bytes apart along M and chunks kFzLbo bytes apart along K,
 // so the operand of tap d (rows d .. d + 127) is the same buffer with its start 16 d bytes later:
 // one copy of the input serves all five taps.  The hidden layers' sums and their ReLU/BF16
-// rounding are those of conv_tc_kernel (same MMAs in the same order), and the last layer adds its
-// products in the order of conv_out_kernel, so the logits are the layer-by-layer path's.
+// rounding are those of conv_tc_kernel (same MMAs in the same order); the last layer sums its
+// products in four partial sums (one per 8-channel chunk), so its rounding differs from the
+// layer-by-layer path's single chain.
 constexpr int kFzRows = kTcRows;             // 132 rows per operand buffer
 constexpr int kFzOut = kTcTile - 12;         // 116 logits per tile
 constexpr int kFzLbo = kFzRows * 16;         // bytes between the chunks of a buffer
 constexpr int kFzBLbo = 32 * 16;             // the same for the 32-row weight operands
 
 struct FzSmem {
-    uint8_t x[2][4 * kFzLbo];       // input windows (the next tile's is copied while this one runs)
-    uint8_t h[2][4 * kFzLbo];       // hidden activations (ping-pong between layers)
+    uint8_t x[4 * kFzLbo];          // input window (the next tile's is copied once layer 1 is done)
+    uint8_t h[4 * kFzLbo];          // hidden activations: each layer's epilogue overwrites its
+                                    // own input once the layer's MMAs have completed
     uint8_t b[3][5][4 * kFzBLbo];   // B_d of the three hidden layers, B_d[o][i] = W[d][i][o]
     float bias[3][32];
     float w4[5 * 32];
@@ -298,7 +301,7 @@ __device__ __forceinline__ void fz_cp_async4(uint32_t dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
 }
 
-__global__ void __launch_bounds__(kTcThreads, 3) cnn_infer_kernel(const uint32_t *__restrict__ feat,
+__global__ void __launch_bounds__(kTcThreads, 4) cnn_infer_kernel(const uint32_t *__restrict__ feat,
                                                                   const float *__restrict__ Wu,
                                                                   float *__restrict__ logits,
                                                                   const SeriesDesc *__restrict__ desc,
@@ -314,6 +317,7 @@ __global__ void __launch_bounds__(kTcThreads, 3) cnn_infer_kernel(const uint32_t
     const int64_t tbeg = ntiles * blockIdx.x / gridDim.x, tend = ntiles * (blockIdx.x + 1) / gridDim.x;
 
     // weights: B_d of the hidden layers (first layer's 18 input channels padded to 32 with zeros)
+#pragma unroll 4
     for (int e = tid; e < 3 * 5 * 32 * 32; e += kTcThreads) {
         const int L = e / 5120, d = (e >> 10) % 5, o = (e >> 5) & 31, i = e & 31;
         float v;
@@ -328,13 +332,12 @@ __global__ void __launch_bounds__(kTcThreads, 3) cnn_infer_kernel(const uint32_t
     for (int e = tid; e < 160; e += kTcThreads) sm.w4[e] = Wu[cnn_off(6) + e];
     if (tid == 0) sm.b4 = Wu[cnn_off(7)];
     // never written by the tiles: input channels 18 .. 31 and hidden rows 128 .. 131
-    for (int e = tid; e < 2 * kFzRows * 7; e += kTcThreads) {
-        const int b = e / (kFzRows * 7), r = (e / 7) % kFzRows, w = 9 + e % 7;
-        *reinterpret_cast<uint32_t *>(sm.x[b] + (w >> 2) * kFzLbo + r * 16 + (w & 3) * 4) = 0u;
+    for (int e = tid; e < kFzRows * 7; e += kTcThreads) {
+        const int r = e / 7, w = 9 + e % 7;
+        *reinterpret_cast<uint32_t *>(sm.x + (w >> 2) * kFzLbo + r * 16 + (w & 3) * 4) = 0u;
     }
-    for (int e = tid; e < 2 * 4 * 4; e += kTcThreads)
-        *reinterpret_cast<uint4 *>(sm.h[e >> 4] + ((e >> 2) & 3) * kFzLbo + (kTcTile + (e & 3)) * 16) =
-            make_uint4(0, 0, 0, 0);
+    if (tid < 16)
+        *reinterpret_cast<uint4 *>(sm.h + (tid >> 2) * kFzLbo + (kTcTile + (tid & 3)) * 16) = make_uint4(0, 0, 0, 0);
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.mbar)));
         asm volatile("fence.mbarrier_init.release.cluster;");
@@ -358,14 +361,14 @@ __global__ void __launch_bounds__(kTcThreads, 3) cnn_infer_kernel(const uint32_t
         while (s + 1 < S && tiles_before[s + 1] <= tile) s++;
         return s;
     };
-    // copy tile `tile`'s input window into x[buf]: feature words (two channels each) 0 .. 8 of the
+    // copy tile `tile`'s input window into x: feature words (two channels each) 0 .. 8 of the
     // rows at positions P .. P + 131, zeros at positions outside [0, T)
-    auto issue_x = [&](int64_t tile, int buf) {
+    auto issue_x = [&](int64_t tile) {
         const int64_t ss = series_of(tile);
         const SeriesDesc d = desc[ss];
         const int P = (int)(tile - tiles_before[ss]) * kFzOut - 8;
         const uint32_t *src = feat + (row_base(d, ss) + 2) * (kFeatC / 2);  // position 0
-        const uint32_t xa = smem_u32(sm.x[buf]);
+        const uint32_t xa = smem_u32(sm.x);
         for (int e = tid; e < kFzRows * 9; e += kTcThreads) {
             const int j = e / 9, w = e - 9 * j, pos = P + j;
             const uint32_t dst = xa + (uint32_t)((w >> 2) * kFzLbo + j * 16 + (w & 3) * 4);
@@ -444,10 +447,9 @@ __global__ void __launch_bounds__(kTcThreads, 3) cnn_infer_kernel(const uint32_t
         asm volatile("tcgen05.fence::after_thread_sync;");
     };
 
-    if (tbeg < tend) issue_x(tbeg, 0);
+    if (tbeg < tend) issue_x(tbeg);
     bool ok = true;
     for (int64_t tile = tbeg; tile < tend && ok; tile++) {
-        const int buf = (int)((tile - tbeg) & 1);
         const int64_t ss = series_of(tile);
         const SeriesDesc d = desc[ss];
         const int P = (int)(tile - tiles_before[ss]) * kFzOut - 8;
@@ -456,38 +458,38 @@ __global__ void __launch_bounds__(kTcThreads, 3) cnn_infer_kernel(const uint32_t
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;");
-        if (tid == 0) issue_layer(sm.x[buf], 0);
-        if (tile + 1 < tend) issue_x(tile + 1, buf ^ 1);  // in flight while this tile runs
+        if (tid == 0) issue_layer(sm.x, 0);
         // hidden layers: layer L's row tid is position P + 2 (L + 1) + tid
 #pragma unroll 1
         for (int L = 0; L < 3 && ok; L++) {
             ok = wait_layer();
             if (!ok) break;
+            if (L == 0 && tile + 1 < tend) issue_x(tile + 1);  // x is free: in flight for the rest
             const int pos = P + 2 * (L + 1) + tid;
-            uint8_t *out = sm.h[L & 1];
-            epilogue(out, L, pos >= 0 && pos < d.T);
-            if (L < 2 && tid == 0) issue_layer(out, L + 1);
+            epilogue(sm.h, L, pos >= 0 && pos < d.T);
+            if (L < 2 && tid == 0) issue_layer(sm.h, L + 1);
         }
         if (!ok) break;
-        // last layer, 32 -> 1, from the third layer's rows tid .. tid + 4 (in sm.h[0])
+        // last layer, 32 -> 1, from the third layer's rows tid .. tid + 4; one partial sum per
+        // 8-channel chunk
         const int pos = P + 8 + tid;
         if (tid < kFzOut && pos < d.T) {
-            float acc = sm.b4;
+            float part[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int dd = 0; dd < 5; dd++) {
 #pragma unroll
                 for (int c = 0; c < 4; c++) {
-                    const uint4 v = *reinterpret_cast<const uint4 *>(sm.h[0] + c * kFzLbo + (tid + dd) * 16);
+                    const uint4 v = *reinterpret_cast<const uint4 *>(sm.h + c * kFzLbo + (tid + dd) * 16);
                     const uint32_t u[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
                     for (int hh = 0; hh < 4; hh++) {
                         const float lo = __uint_as_float(u[hh] << 16), hi = __uint_as_float(u[hh] & 0xffff0000u);
-                        acc = fmaf(lo, sm.w4[dd * 32 + c * 8 + 2 * hh], acc);
-                        acc = fmaf(hi, sm.w4[dd * 32 + c * 8 + 2 * hh + 1], acc);
+                        part[c] = fmaf(lo, sm.w4[dd * 32 + c * 8 + 2 * hh], part[c]);
+                        part[c] = fmaf(hi, sm.w4[dd * 32 + c * 8 + 2 * hh + 1], part[c]);
                     }
                 }
             }
-            logits[row_base(d, ss) + 2 + pos] = acc;
+            logits[row_base(d, ss) + 2 + pos] = sm.b4 + ((part[0] + part[1]) + (part[2] + part[3]));
         }
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
@@ -524,7 +526,7 @@ cudaError_t cnn_infer(const CnnState &W, const uint16_t *feat, float *logits, co
     }
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t grid = std::min<int64_t>(ntiles, (int64_t)sms * 3);
+    const int64_t grid = std::min<int64_t>(ntiles, (int64_t)sms * 4);
     cnn_infer_kernel<<<(unsigned)grid, kTcThreads, sizeof(FzSmem), st>>>(
         reinterpret_cast<const uint32_t *>(feat), W.used, logits, desc, tiles_before, S, ntiles, wait_limit_ns,
         status, gate);
