@@ -215,7 +215,7 @@ def main():
     stream = torch.cuda.current_stream(dev)
     graph = args.workload == "uneven"
     tune_s = None
-    if graph:  # the uneven workload: autotuned tiles per shape bucket, graph replay per step
+    if graph and not args.kpt:  # the uneven workload: autotuned tiles per shape bucket, graph replay per step
         t0 = time.perf_counter()
         eng.autotune(d_samples, b.offsets, b.steps, stream=stream)
         tune_s = time.perf_counter() - t0
@@ -290,7 +290,8 @@ def main():
             tiles[key] = eng.autotune_get(int(T_), int(m_))
         line["cuda_graph"] = True
         line["autotune"] = {"seconds": tune_s, "tiles": dict(sorted(tiles.items())),
-                            "tile_codes": "1/2/4 = groups of 32 splits per work item, 8 = run sweep"}
+                            "tile_codes": "1/2/4 = groups of 32 splits per work item, 8 = run sweep",
+                            "forced_tile": args.kpt or None}
         # the learned path on the same batch (the network trained on the three-level recipe; its
         # window and grid probes serve the series scanned in slices), direct calls with the same
         # tiles, answers compared with the plain call's on the device

@@ -1164,19 +1164,12 @@ int ensure_cnn_ws(mt4g_ctx *c, size_t bytes) {
     if (bytes <= c->cnn_ws_bytes) return MT4G_OK;
     if (c->capturing) return fail(c, MT4G_ECUDA, "workspace growth during graph capture");
     if (c->have_last) CUDA_TRY(c, cudaStreamSynchronize(c->last_stream));
-    if (c->graph_exec) {
-        cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph_stream) CUDA_TRY(c, cudaStreamSynchronize(c->graph_stream));
+    if (c->graph_exec) {  // the captured graph points into the old workspace; its stream,
+        cudaGraphExecDestroy(c->graph_exec);  // events and pinned staging stay for the next capture
         c->graph_exec = nullptr;
     }
     if (c->cnn_ws) cudaFree(c->cnn_ws);
-    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
-    if (c->graph_pin) cudaFreeHost(c->graph_pin);
-    if (c->graph_stream) {
-        cudaStreamSynchronize(c->graph_stream);
-        cudaStreamDestroy(c->graph_stream);
-        cudaEventDestroy(c->graph_in);
-        cudaEventDestroy(c->graph_out);
-    }
     c->cnn_ws = nullptr;
     c->cnn_ws_bytes = 0;
     const size_t want = bytes + bytes / 8;

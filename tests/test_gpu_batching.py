@@ -90,6 +90,27 @@ def test_graph_replay_scan_and_learned(eng):
     eng.set_option(mt4g.OPT_CONF_MIN_PPM, 900000)
 
 
+def test_graph_after_proposal_workspace_growth(eng):
+    """A learned call that grows the proposal workspace after a graph was captured drops the
+    graph (it points into the old workspace) but keeps its stream, events and pinned staging:
+    the next graph call recaptures on them, and closing the engine frees each once."""
+    small, big = synth.generate(2, 44, 8), synth.generate(2, 45, 64)
+    ds, db = mt4g.to_device_samples(small.samples), mt4g.to_device_samples(big.samples)
+    eng.cnn_init(4)
+    eng.set_option(mt4g.OPT_GRAPH, 1)
+    _, g1 = _seg(eng, ds, small)
+    eng.set_option(mt4g.OPT_GRAPH, 0)
+    _, l1 = _seg(eng, db, big, mode=mt4g.MODE_LEARNED)  # first proposal workspace, sized for 64 series
+    eng.set_option(mt4g.OPT_GRAPH, 1)
+    r, g2 = _seg(eng, ds, small)
+    _, g3 = _seg(eng, ds, small, out=r)
+    eng.set_option(mt4g.OPT_GRAPH, 0)
+    _same(g1, g2)
+    _same(g1, g3)
+    _oracle_same(small, g1)
+    _oracle_same(big, l1)
+
+
 def test_autotune_keeps_results_and_roundtrips(eng, tmp_path):
     b = synth.generate(3, 2, 300)
     keep = [s for s in range(300) if float(b.steps[s]) ** 2 * float(b.m[s]) < 3e8][:120]
