@@ -17,10 +17,10 @@
 
 namespace mt4g {
 
-constexpr int kSortThreads = 512;
+constexpr int kSortThreads = 256;  // four CTAs per SM
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortItems = 8;
-constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 samples per tile
+constexpr int kSortTile = kSortThreads * kSortItems;  // 2048 samples per tile
 
 constexpr int kScanThreads = 256;  // CTA of the persistent kernel: 8 independent warps
 

@@ -9,7 +9,7 @@
 // per sample; otherwise values and 16-bit labels move separately.  The first read
 // also counts the first digit, and each pass counts the next one while it ranks.
 //
-// Within a 4096-sample tile, each warp ranks its 256 samples by digit-peer masks
+// Within a 2048-sample tile, each warp ranks its 256 samples by digit-peer masks
 // (stable: item-major, then lane order), per-warp digit counts are scanned across warps, the tile is staged in shared memory in sorted order and written out so
 // that consecutive positions of a digit go to consecutive addresses; a running
 // per-digit base carries the order across tiles.  The last step writes the labels
@@ -94,6 +94,9 @@ __device__ __forceinline__ uint32_t div_step(uint32_t e, uint32_t m, float inv_m
     return t;
 }
 
+constexpr int kCountWords = 11552;  // the counting table (46 KB; four CTAs per SM)
+constexpr int kSortFieldWords = kSortWarps * 256 + 5 * 256 + kSortTile + kSortTile / 2 + 32;
+
 struct SortSmem {
     uint32_t wc[kSortWarps][256];  // per-warp digit counts -> tile-local offsets
     uint32_t hist[256];            // digit counts of the current pass (whole series)
@@ -104,6 +107,8 @@ struct SortSmem {
     uint32_t key[kSortTile];       // tile staged in sorted order
     uint16_t lab[kSortTile];
     uint32_t tmp[32];
+    // the counting path uses the whole struct as kFastSpan 32-bit counters
+    uint32_t spare[kCountWords > kSortFieldWords ? kCountWords - kSortFieldWords : 1];
 };
 
 // LSD passes over one series.  COMP: keys are (value << 16) | step (value < 2^16), the
@@ -229,7 +234,8 @@ __device__ void lsd_passes(SortSmem &sm, int passes, const uint32_t *__restrict_
 }
 
 // Values per series the counting path can index: the sort's shared memory as 32-bit counters.
-constexpr uint32_t kFastSpan = (uint32_t)(sizeof(SortSmem) / sizeof(uint32_t));
+constexpr uint32_t kFastSpan = (uint32_t)kCountWords;
+static_assert(kFastSpan * sizeof(uint32_t) <= sizeof(SortSmem), "counting table fits the sort's shared memory");
 // The counting table's base is guessed from the series' first sample, this far below it (a
 // latency series usually starts at its smallest latencies); a value outside the table sends the
 // series to a recount from its true minimum.
@@ -481,7 +487,7 @@ __device__ void digit0_minmax(SortSmem &sm, const uint32_t *__restrict__ in, int
     block_minmax(vmin, vmax);
 }
 
-__global__ void __launch_bounds__(kSortThreads, 2)
+__global__ void __launch_bounds__(kSortThreads, 4)
 sort_series_kernel(const uint32_t *__restrict__ samples, SeriesDesc *__restrict__ desc,
                    const int32_t *__restrict__ order, uint32_t *__restrict__ keyA, uint32_t *__restrict__ keyB,
                    uint16_t *__restrict__ labA, uint16_t *__restrict__ labB, int32_t *__restrict__ runs,
