@@ -331,6 +331,21 @@ def main():
             "agreement": float(same_sl.float().mean().item()), "evals": evals_sl,
             "certified_segments": stats_sl["certified"], "refined_segments": stats_sl["refined"],
             "stage_ms": dict(zip(STAGES, np.asarray(stages_sl).mean(axis=0).tolist()))}
+        # window-only scans of the swept series (no certification): agreement with the full
+        # scan measured per series, low-confidence and non-significant series fall back
+        eng.set_option(mt4g.OPT_LEARNED_WINDOWS, 1)
+        try:
+            t_w, out_w, _, stages_w, evals_w, _ = timed(mode, args.steps, 1)
+        finally:
+            eng.set_option(mt4g.OPT_LEARNED_WINDOWS, 0)
+        same_w = torch.ones(S, dtype=torch.bool, device=dev)
+        for a_, c_ in zip(out_plain[1:6], out_w[1:6]):
+            same_w &= (a_ == c_).reshape(S, -1).all(dim=1)
+        line["learned_windows"] = {
+            "value": S * world * args.steps / t_w, "ms_per_step": t_w / args.steps * 1e3,
+            "speedup_vs_plain": t_plain / t_w, "agreement": float(same_w.float().mean().item()),
+            "fallback_rate": float(out_w[6].float().mean().item()), "evals": evals_w,
+            "stage_ms": dict(zip(STAGES, np.asarray(stages_w).mean(axis=0).tolist()))}
         line.update({"plain_value": plain_value, "plain_ms_per_step": t_plain / args.steps * 1e3,
                      "speedup_vs_plain": value / plain_value, "agreement": float(same.float().mean().item()),
                      "fallback_rate": float(fb.float().mean().item()),

@@ -96,6 +96,15 @@ extern "C" {
                                     gives a D strictly below the best D so far is not evaluated (its
                                     samples still move).  The answers are those of the full scan;
                                     mt4g_last_work counts only the evaluated pairs.  Off by default. */
+#define MT4G_OPT_LEARNED_WINDOWS 10 /* 1: in MT4G_MODE_LEARNED, a series the run sweep takes and whose
+                                    window mass reaches the threshold is scanned only at the splits
+                                    of its windows (|k - c| <= half width), with no certification:
+                                    the exact D of those splits decides each segment, a segment
+                                    without window splits is not split, and a series whose top
+                                    level has no significant window split falls back to the full
+                                    scan (fallback = 1).  The answers can then differ from
+                                    MT4G_MODE_FULL where a change point lies outside every window;
+                                    the agreement is measured, not guaranteed.  Off by default. */
 
 typedef struct mt4g_ctx mt4g_ctx;
 
@@ -152,8 +161,11 @@ int mt4g_ks_scan(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offsets,
  *   at the windows' splits and at up to 32 grid splits; each gap between grid splits gets
  *   a bound on D from its two end columns, and the gaps whose bound might reach the best
  *   D found are scanned exactly.  The results are therefore those of MT4G_MODE_FULL.
+ *   With MT4G_OPT_LEARNED_WINDOWS the series the run sweep takes are instead scanned only
+ *   at their window splits (see the option), and the answers are those of the windows.
  * fallback: DEVICE int32 [S] or NULL; 1 where the series took the full scan (low
- *   confidence or the run sweep; always 0 outside learned mode).
+ *   confidence, the run sweep without MT4G_OPT_LEARNED_WINDOWS, or a window-only top level
+ *   without a significant split; always 0 outside learned mode).
  * crit: DEVICE double [S * max_cp] or NULL; beside each reported change point, the critical
  *   value of D at level alpha for the two sample sizes of the split that created it (Eq. 1,
  *   read with the minus sign its printed radicand lost and the natural log):

@@ -27,6 +27,7 @@ OPT_CONF_MIN_PPM = 6
 OPT_GRAPH = 7
 OPT_CHECKS = 8
 OPT_SWEEP_SKIP = 9
+OPT_LEARNED_WINDOWS = 10
 SCAN_SWEEP = 8  # MT4G_OPT_SCAN_KPT value of the run sweep
 MAX_STEPS = 32768
 FEAT_CHANNELS = 18

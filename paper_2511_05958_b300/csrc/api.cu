@@ -75,6 +75,7 @@ struct mt4g_ctx {
 
     bool checks = false;  // MT4G_OPT_CHECKS: consistency check of the sort's output
     bool sweep_skip = false;  // MT4G_OPT_SWEEP_SKIP: exact bound skipping in the run sweep
+    bool learned_windows = false;  // MT4G_OPT_LEARNED_WINDOWS: window-only scans of swept series
 
     // CUDA-graph replay of identical calls (MT4G_OPT_GRAPH)
     bool use_graph = false;
@@ -666,6 +667,10 @@ int mt4g_set_option(mt4g_ctx *c, int option, int64_t value) {
         c->sweep_skip = value != 0;
         return MT4G_OK;
     }
+    if (option == MT4G_OPT_LEARNED_WINDOWS) {
+        c->learned_windows = value != 0;
+        return MT4G_OK;
+    }
     if (option == MT4G_OPT_WINDOWS) {
         if (value < 1 || value > 8) return fail(c, MT4G_EINVAL, "windows must be 1..8");
         c->n_win = (int32_t)value;
@@ -773,6 +778,7 @@ static int segment_body(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *o
     const int epoch = enqueue_pipeline(ctx, samples, P, R, B, st);
     if (epoch < 0) return epoch;
     R.mode = P.learned ? kRunLearned : kRunSegment;
+    R.win_only = P.learned && ctx->learned_windows && R.rk ? 1 : 0;
     R.alpha = alpha;
     // Eq. 1's constant -1/2 ln(alpha / 2), once on the host; each accepted split multiplies it
     // by (n_L + n_R) / (n_L n_R) (critical value beside the change point)
@@ -894,6 +900,7 @@ uint64_t call_key(const mt4g_ctx *ctx, int entry, const void *samples, const int
     h = fnv_val(h, ctx->forced_kpt);
     h = fnv_val(h, ctx->checks);
     h = fnv_val(h, ctx->sweep_skip);
+    h = fnv_val(h, ctx->learned_windows);
     h = fnv_val(h, ctx->cnn_version);
     for (int i = 0; i < n_outs; i++) h = fnv_val(h, outs[i]);
     if (S > 0 && offsets && steps) {
@@ -1558,8 +1565,9 @@ int enqueue_proposals(mt4g_ctx *ctx, const uint32_t *samples, Plan &P, Buffers &
     rc = upload_cnn_tables(ctx, P.desc, C, &ntiles, st);
     if (rc) return rc;
     // in sweep calls the sort counted the series the sweep does not take: only they use the
-    // proposals, and with none the proposal kernels return at once
-    const unsigned long long *gate = P.use_sweep ? &B.q->unswept : nullptr;
+    // proposals (unless swept series are scanned in their windows), and with none the proposal
+    // kernels return at once
+    const unsigned long long *gate = P.use_sweep && !ctx->learned_windows ? &B.q->unswept : nullptr;
     CUDA_TRY(ctx, launch_summaries(samples, B.desc, S, C.feat, st, gate));
     CUDA_TRY(ctx, cnn_prepare(ctx->cnn, st));
     CUDA_TRY(ctx, cnn_infer(ctx->cnn, C.feat, C.A.logits, B.desc, C.infer_before, S, C.ninfer, ctx->wait_limit_ns,

@@ -148,10 +148,13 @@ struct RunParams {
     const int32_t *win_center;  // [S * n_win], -1 = none
     int32_t n_win;
     int32_t half;               // window slice covers [c - half, c - half + 31]
-    const int32_t *fallback;    // [S]: 1 = the series takes the plain path
+    int32_t *fallback;          // [S]: 1 = the series takes the plain path (set again by the
+                                //      window-only scan when its top level is not significant)
     CertRecord *recs;
     int32_t sweep_warps;        // warps of the launch: the sweep's parts per segment follow from them
     int32_t sweep_skip;         // 1: the run sweep skips splits by the exact bound (MT4G_OPT_SWEEP_SKIP)
+    int32_t win_only;           // 1: learned calls scan swept series only at their window splits
+                                //    (MT4G_OPT_LEARNED_WINDOWS)
     int32_t top_parts;          // parts of a top-level run-sweep segment (planned on the host)
 };
 

@@ -683,6 +683,46 @@ __device__ __forceinline__ void sweep_apply_step(SweepStage &ss, const uint16_t 
     }
 }
 
+// Move the samples of steps [t0, t1) to the left part: their run indices are contiguous, so
+// they are read as one range, 8 loads in flight per lane (8-byte loads in the vector form, 1024
+// samples a round; else 2-byte loads, 256 a round).  Few registers: the lane block's C values
+// stay live in registers around it (16 loads in flight make the learned kernels spill).
+template <bool VEC>
+__device__ void sweep_move_range(SweepStage &ss, const uint16_t *__restrict__ rk, int64_t t0, int64_t t1, int m,
+                                 uint32_t H, int lane) {
+    const int64_t f0 = t0 * m, e1 = t1 * m;
+    if constexpr (VEC) {
+        const uint2 *src = reinterpret_cast<const uint2 *>(rk);
+        for (int64_t e0 = f0; e0 < e1; e0 += 1024) {
+            uint2 x8[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const int64_t e = e0 + 128 * q + 4 * lane;
+                x8[q] = e < e1 ? __ldg(src + (e >> 2)) : make_uint2(0u, 0u);
+            }
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const bool act = e0 + 128 * q + 4 * lane < e1;
+                lc_add(ss, x8[q].x & 0xffffu, H, act);
+                lc_add(ss, x8[q].x >> 16, H, act);
+                lc_add(ss, x8[q].y & 0xffffu, H, act);
+                lc_add(ss, x8[q].y >> 16, H, act);
+            }
+        }
+    } else {
+        for (int64_t e0 = f0; e0 < e1; e0 += 256) {
+            uint32_t r8[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const int64_t e = e0 + 32 * q + lane;
+                r8[q] = e < e1 ? (uint32_t)__ldg(rk + e) : 0u;
+            }
+#pragma unroll
+            for (int q = 0; q < 8; q++) lc_add(ss, r8[q], H, e0 + 32 * q + lane < e1);
+        }
+    }
+}
+
 // Four runs of a lane's block: running l sum hc, values hc - a C relative to the run before
 // the block, their max and min (three-input integer max / min).
 __device__ __forceinline__ void sweep_eval4(const uint4 q, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
@@ -705,14 +745,57 @@ __device__ __forceinline__ void sweep_eval4(const uint4 q, uint32_t c0, uint32_t
 // samples of steps lo .. A - 1 are moved left first); every lane gets it.  `nonempty` = U', the
 // runs with in-segment samples; `nev` = the splits evaluated.
 //
-// SKIP: exact bound skipping.  Moving one step's m samples changes every v(c) by H s(c) - C(c),
+// How the run sweep walks the splits: every split in order (kWalkAll); exact bound skipping
+// (kWalkSkip); only the window splits of a window-only learned scan (kWalkWindows, for items
+// with `win`, else every split).
+constexpr int kWalkAll = 0, kWalkSkip = 1, kWalkWindows = 2;
+
+// kWalkSkip: exact bound skipping.  Moving one step's m samples changes every v(c) by H s(c) - C(c),
 // s(c) <= m and C(c) <= m H, so |g_{k+j} - g_k| <= j m H.  A split whose bound from the last
 // evaluated split e, g_e + (k - e) m H, gives a D strictly below the best D found so far,
 //     (g_e + (k - e) m H) a_b (H - a_b) < g_b a_k (H - a_k)        (128-bit products),
 // can be neither the argmax nor tie with it, so it is not evaluated; its samples still move.
-template <bool VEC, bool SKIP>
+// Window-only learned scan (MT4G_OPT_LEARNED_WINDOWS): split k of series `series` is a
+// candidate when |k - c| <= half for one of its window centres c (c < 0: no window).
+// The first window split in [A, B]; B + 1 when there is none.
+__device__ __forceinline__ int first_window_split(const RunParams &P, int series, int A, int B) {
+    const int32_t *c = P.win_center + (int64_t)series * P.n_win;
+    int first = B + 1;
+    for (int w = 0; w < P.n_win; w++) {
+        const int cw = __ldg(c + w);
+        if (cw < 0) continue;
+        const int a = max(A, cw - P.half), b = min(B, cw + P.half);
+        if (a <= b && a < first) first = a;
+    }
+    return first;
+}
+
+// The first merged window interval [a, b] of series `series` within [from, B]: a is the first
+// window split >= from, b the end of the union of the windows that overlap or touch [a, b].
+// False when no window split is left.  Every lane computes the same.
+__device__ __forceinline__ bool window_interval(const RunParams &P, int series, int from, int B, int &a, int &b) {
+    a = first_window_split(P, series, from, B);
+    if (a > B) return false;
+    const int32_t *c = P.win_center + (int64_t)series * P.n_win;
+    b = a;
+    for (bool grew = true; grew;) {
+        grew = false;
+        for (int w = 0; w < P.n_win; w++) {
+            const int cw = __ldg(c + w);
+            if (cw < 0) continue;
+            const int lw = cw - P.half, hw = min(B, cw + P.half);
+            if (lw <= b + 1 && hw > b) {
+                b = hw;
+                grew = true;
+            }
+        }
+    }
+    return true;
+}
+
+template <bool VEC, int WALK>
 __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int hi, int A, int B, SweepStage &ss,
-                           int &bk, uint64_t &bg, int &nonempty, int &nev) {
+                           int &bk, uint64_t &bg, int &nonempty, int &nev, bool win = false, int series = 0) {
     const int lane = threadIdx.x & 31;
     const int U = d.nruns, m = d.m;
     const uint16_t *__restrict__ rk = P.rk + d.off;
@@ -815,11 +898,7 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
     for (int w = lane; w < 32 * Rs; w += 32) ss.l[w] = 0u;
     __syncwarp();
 
-    for (int t = lo; t < A; t++) {
-        StepBuf<VEC> buf;
-        sweep_load_step<VEC>(rk, t, m, lane, buf);
-        sweep_apply_step<VEC>(ss, rk, t, m, H, lane, buf);
-    }
+    sweep_move_range<VEC>(ss, rk, lo, A, m, H, lane);
     const uint4 *lq = reinterpret_cast<const uint4 *>(&ss.l[lane * Rs]);
     // run indices two steps ahead (global loads in flight over two splits); the layout
     // positions of step k's samples are looked up at the top of split k and used by its moves
@@ -845,11 +924,12 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
         const uint32_t gl = max((uint32_t)max(bmax, 0), (uint32_t)max(-bmin, 0));
         return __reduce_max_sync(kFull, gl);
     };
-    // without skipping the argmax is taken 32 splits at a time (lane j holds split kb + j)
-    auto finish = [&](int kp) {
+    // without skipping the argmax is taken 32 splits at a time (lane j holds split kb + j);
+    // kend ends the current range of consecutive splits
+    auto finish = [&](int kp, int kend) {
         const uint32_t g = split_g();
         if (lane == kp - kb) gk = g;
-        if (kp - kb == 31 || kp == B) {
+        if (kp - kb == 31 || kp == kend) {
             const int kk = kb + lane;
             if (kk <= kp && better(kk, (uint64_t)gk, bk, bg, lo, hi)) {
                 bk = kk;
@@ -887,7 +967,8 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
         p_mn = mn;
     };
     nev = 0;
-    if constexpr (SKIP) {
+    if constexpr (WALK == kWalkSkip) {
+        {
         // Walk: evaluate split k; the bound from it, with the best so far, excludes a run of the
         // following splits (lane i tests split k + 1 + i, a ballot gives the run's length); the
         // steps up to the next split to evaluate move left in one pass, with no per-split work.
@@ -922,21 +1003,23 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
             // every lane has read l for split k: steps k .. next - 1 move left
             __syncwarp();
             sweep_apply_step<VEC>(ss, rk, k, m, H, lane, cur);  // step k, loaded during split k
-            for (int t = k + 1; t < next; t++) {
-                StepBuf<VEC> b;
-                sweep_load_step<VEC>(rk, t, m, lane, b);
-                sweep_apply_step<VEC>(ss, rk, t, m, H, lane, b);
-            }
+            sweep_move_range<VEC>(ss, rk, k + 1, next, m, H, lane);
             k = next;
             if (k <= B) sweep_load_step<VEC>(rk, k, m, lane, cur);
         }
         __syncwarp();
         return;
-    } else {
+        }
+    }
+    // every split of [Ai, Bi] in order, software-pipelined: run indices two steps ahead, split
+    // k - 1 finished while split k's first loads are in flight; step k moves left after split k
+    // for k < Bi (step Bi stays on the right)
+    auto sweep_range = [&](int Ai, int Bi) {
+        kb = Ai;
         StepBuf<VEC> nxt, nxt2;
-        sweep_load_step<VEC>(rk, A, m, lane, nxt);
-        if (A + 1 <= B) sweep_load_step<VEC>(rk, A + 1, m, lane, nxt2);
-        for (int k = A; k <= B; k++) {
+        sweep_load_step<VEC>(rk, Ai, m, lane, nxt);
+        if (Ai + 1 <= Bi) sweep_load_step<VEC>(rk, Ai + 1, m, lane, nxt2);
+        for (int k = Ai; k <= Bi; k++) {
             const StepBuf<VEC> cur = nxt;
             uint32_t pos0 = 0, pos1 = 0, pos2 = 0, pos3 = 0;
             if (VEC && 4 * lane < m) {
@@ -946,15 +1029,15 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
                 pos3 = ss.map[cur.v[1] >> 16];
             }
             nxt = nxt2;
-            if (k + 2 <= B) sweep_load_step<VEC>(rk, k + 2, m, lane, nxt2);
+            if (k + 2 <= Bi) sweep_load_step<VEC>(rk, k + 2, m, lane, nxt2);
             __syncwarp();
-            if (k > A) finish(k - 1);
+            if (k > Ai) finish(k - 1, Bi);
             nev++;
             evaluate(k);
             // every lane has read l for split k: step k's samples move left now (reductions the warp
             // does not wait for)
             __syncwarp();
-            if (k < B) {
+            if (k < Bi) {
                 if constexpr (VEC) {
                     if (4 * lane < m) {
                         atomicAdd(&ss.l[pos0], H);
@@ -977,10 +1060,27 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
                 }
             }
         }
-        finish(B);
-        warp_best(bk, bg, lo, hi);
-        __syncwarp();
+        finish(Bi, Bi);
+    };
+    if (WALK == kWalkWindows && win) {
+        // window-only scan: the merged window intervals within [A, B] (A is the first window
+        // split, the steps before it moved in the setup); the steps between intervals move in one
+        // pass each
+        int from = A, prev = -1, a = 0, b = 0;
+        while (window_interval(P, series, from, B, a, b)) {
+            if (prev >= 0) {
+                __syncwarp();
+                sweep_move_range<VEC>(ss, rk, prev, a, m, H, lane);  // steps prev .. a - 1
+            }
+            sweep_range(a, b);
+            prev = b;
+            from = b + 1;
+        }
+    } else {
+        sweep_range(A, B);
     }
+    warp_best(bk, bg, lo, hi);
+    __syncwarp();
 }
 
 // Reserve `tot` queue slots and count them as pending (one lane).  Returns the first slot,
@@ -1044,6 +1144,27 @@ __device__ void push_plain(const RunParams &P, const SeriesDesc &d, int series, 
     for (int c = lane; c < nch; c += 32) st_release_u32((uint32_t *)P.ready + base + c, epoch);
 }
 
+// Window-only scan of a swept segment (MT4G_OPT_LEARNED_WINDOWS; all lanes, same arguments):
+// its window splits, by the sweep.  A segment without any is a leaf, and a series without any at
+// its top level takes the full scan.
+__device__ __noinline__ void push_window_segment(const RunParams &P, const SeriesDesc &d, int series, int lo, int hi,
+                                                 uint32_t epoch, int want_parts) {
+    const int lane = threadIdx.x & 31;
+    const int A = lo + P.min_seg, B = hi - P.min_seg;
+    int fw = 0;
+    if (lane == 0) fw = first_window_split(P, series, A, B);
+    fw = __shfl_sync(kFull, fw, 0);
+    if (fw > B) {
+        if (lo != 0 || hi != d.T) return;
+        if (lane == 0) {
+            P.fallback[series] = 1;
+            __threadfence();
+        }
+        __syncwarp();
+    }
+    push_plain(P, d, series, lo, hi, epoch, want_parts);
+}
+
 // Push the work for segment [lo, hi) (all lanes of a warp call it with the same arguments).
 // Plain series, and learned segments with no window centred at least half/2 inside their
 // splits: the full scan (push_plain).  Other learned segments: a probe group of the window
@@ -1056,6 +1177,10 @@ __device__ __noinline__ void push_segment(const RunParams &P, const SeriesDesc &
     const bool learned = P.mode == kRunLearned && !P.fallback[series];
     if (!learned) {
         push_plain(P, d, series, lo, hi, epoch, want_parts);
+        return;
+    }
+    if (P.win_only && eff_kpt(P, d, hi - lo) == 0) {
+        push_window_segment(P, d, series, lo, hi, epoch, want_parts);
         return;
     }
     // a probe only pays where a window is centred well inside the segment; elsewhere (in
@@ -1102,8 +1227,11 @@ __device__ __noinline__ void push_segment(const RunParams &P, const SeriesDesc &
 __device__ __noinline__ void finish_segment(const RunParams &P, const SeriesDesc &d, int series, int lo, int hi, int k,
                                uint64_t g, uint32_t epoch) {
     const int lane = threadIdx.x & 31;
-    int accept = 0;
-    if (lane == 0) {
+    int accept = 0, rescan = 0;
+    if (lane == 0 && k == kNoK) {
+        // a window-only segment without window splits (pushed only at the top level, by parts
+        // whose ranges miss the windows): not significant
+    } else if (lane == 0) {
         const int64_t m = d.m;
         const int64_t a = k - lo, b = hi - k;
         const int64_t num = m * (int64_t)g;
@@ -1128,7 +1256,18 @@ __device__ __noinline__ void finish_segment(const RunParams &P, const SeriesDesc
             accept = 1;
         }
     }
+    if (lane == 0 && !accept && P.mode == kRunLearned && P.win_only && lo == 0 && hi == d.T &&
+        !P.fallback[series] && eff_kpt(P, d, hi - lo) == 0) {
+        // window-only top level without a significant split: the series falls back to the full scan
+        P.fallback[series] = 1;
+        __threadfence();
+        rescan = 1;
+    }
     accept = __shfl_sync(kFull, accept, 0);
+    if (__shfl_sync(kFull, rescan, 0)) {
+        push_segment(P, d, series, lo, hi, epoch);  // the series' flag now routes it to the full scan
+        return;
+    }
     if (!accept) return;
     push_segment(P, d, series, lo, k, epoch);
     push_segment(P, d, series, k, hi, epoch);
@@ -1253,8 +1392,9 @@ __device__ void slice_best(const RunParams &P, const SeriesDesc &d, int lo, int 
 // SWEEP = true adds the run sweep: each warp's shared memory then holds a SweepStage (for
 // up to kSweepMaxRuns runs), launched as CTAs of kSweepThreads; without it, the smaller
 // slice staging allows more resident warps.
-// SKIP (with SWEEP) compiles the run sweep with exact bound skipping (MT4G_OPT_SWEEP_SKIP).
-template <bool LEARNED, bool SWEEP, bool SKIP = false>
+// WALK (with SWEEP) picks how the run sweep walks the splits: all of them, exact bound skipping
+// (MT4G_OPT_SWEEP_SKIP), or window-only learned scans (MT4G_OPT_LEARNED_WINDOWS).
+template <bool LEARNED, bool SWEEP, int WALK = kWalkAll>
 __global__ void __launch_bounds__(SWEEP ? kSweepThreads : kScanThreads, SWEEP ? 8 : 4)
     queue_kernel(RunParams P, uint32_t epoch) {
     using Smem = typename std::conditional<SWEEP, WarpSmem, WarpStage>::type;
@@ -1329,8 +1469,22 @@ __global__ void __launch_bounds__(SWEEP ? kSweepThreads : kScanThreads, SWEEP ? 
                     SweepStage &ss = *reinterpret_cast<SweepStage *>(&s_stage[warp]);
                     const bool vec = (d.off & 3) == 0 && (d.m & 3) == 0;
                     int nev = 0;
-                    if (vec) sweep_best<true, SKIP>(P, d, lo, hi, it.k0, it.klim, ss, bk, bg, nonempty, nev);
-                    else sweep_best<false, SKIP>(P, d, lo, hi, it.k0, it.klim, ss, bk, bg, nonempty, nev);
+                    // window-only learned scan: evaluate only the item's window splits
+                    bool win = false;
+                    int k0 = it.k0;
+                    if (LEARNED && WALK == kWalkWindows && P.win_only && P.mode == kRunLearned &&
+                        *(volatile const int32_t *)(P.fallback + it.series) == 0) {
+                        win = true;
+                        k0 = first_window_split(P, it.series, it.k0, it.klim);
+                    }
+                    if (k0 > it.klim) {
+                        bk = kNoK;  // no window split in this part's range
+                        bg = 0;
+                    } else if (vec) {
+                        sweep_best<true, WALK>(P, d, lo, hi, k0, it.klim, ss, bk, bg, nonempty, nev, win, it.series);
+                    } else {
+                        sweep_best<false, WALK>(P, d, lo, hi, k0, it.klim, ss, bk, bg, nonempty, nev, win, it.series);
+                    }
                     my_evals += (unsigned long long)nev * (unsigned long long)nonempty;
                     my_swept += it.chunk == 0;
                 } else {
@@ -1453,7 +1607,7 @@ __global__ void init_learned_kernel(RunParams P, const float *__restrict__ conf,
     const SeriesDesc d = P.desc[s];
     // the run sweep's cost per split is below the probes': series it takes are scanned in full
     const bool swept = P.rk != nullptr && d.kpt == 0 && d.nruns <= kSweepMaxRuns;
-    if (lane == 0) fallback_out[s] = (conf[s] < conf_min || swept) ? 1 : 0;
+    if (lane == 0) fallback_out[s] = (conf[s] < conf_min || (swept && !P.win_only)) ? 1 : 0;
     __syncwarp();
     __threadfence_block();
     push_segment(P, d, (int)s, 0, d.T, epoch, P.top_parts);
@@ -1513,31 +1667,37 @@ int queue_grid(int device) {
 }
 
 int queue_grid_sweep(int device) {
-    int sms = 0, per_sm = 0, per_sm_l = 0;
+    int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
-    int per_sm_s = 0, per_sm_ls = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, queue_kernel<false, true>, kSweepThreads, 0) !=
+    // one grid for every sweep instantiation: the smallest residency among them
+    int per[5] = {0, 0, 0, 0, 0};
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[0], queue_kernel<false, true>, kSweepThreads, 0) !=
             cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_l, queue_kernel<true, true>, kSweepThreads, 0) !=
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[1], queue_kernel<true, true>, kSweepThreads, 0) !=
             cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_s, queue_kernel<false, true, true>, kSweepThreads, 0) !=
-            cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_ls, queue_kernel<true, true, true>, kSweepThreads, 0) !=
-            cudaSuccess)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[2], queue_kernel<false, true, kWalkSkip>, kSweepThreads,
+                                                      0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[3], queue_kernel<true, true, kWalkSkip>, kSweepThreads,
+                                                      0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[4], queue_kernel<true, true, kWalkWindows>, kSweepThreads,
+                                                      0) != cudaSuccess)
         return 0;
-    per_sm = std::min(std::min(per_sm, per_sm_l), std::min(per_sm_s, per_sm_ls));
+    int per_sm = per[0];
+    for (int i = 1; i < 5; i++) per_sm = std::min(per_sm, per[i]);
     return sms * (per_sm > 0 ? per_sm : 1);
 }
 
 cudaError_t launch_queue_run(const RunParams &P, int grid, uint32_t epoch, cudaStream_t st) {
-    if (P.mode == kRunLearned && P.rk && P.sweep_skip)
-        queue_kernel<true, true, true><<<grid, kSweepThreads, 0, st>>>(P, epoch);
+    if (P.mode == kRunLearned && P.rk && P.win_only)
+        queue_kernel<true, true, kWalkWindows><<<grid, kSweepThreads, 0, st>>>(P, epoch);
+    else if (P.mode == kRunLearned && P.rk && P.sweep_skip)
+        queue_kernel<true, true, kWalkSkip><<<grid, kSweepThreads, 0, st>>>(P, epoch);
     else if (P.mode == kRunLearned && P.rk)
         queue_kernel<true, true><<<grid, kSweepThreads, 0, st>>>(P, epoch);
     else if (P.mode == kRunLearned)
         queue_kernel<true, false><<<grid, kScanThreads, 0, st>>>(P, epoch);
     else if (P.rk && P.sweep_skip)
-        queue_kernel<false, true, true><<<grid, kSweepThreads, 0, st>>>(P, epoch);
+        queue_kernel<false, true, kWalkSkip><<<grid, kSweepThreads, 0, st>>>(P, epoch);
     else if (P.rk)
         queue_kernel<false, true><<<grid, kSweepThreads, 0, st>>>(P, epoch);
     else

@@ -430,3 +430,36 @@ def test_training_checkpoint_and_resume(tmp_path):
     e.close()
     assert np.isfinite(w30).all() and not np.array_equal(w20, w30)
     assert json.load(open(out + ".ckpt.json"))["step"] == 30
+
+
+@pytest.mark.parametrize("trained", [True, False])
+def test_window_only_scan_matches_its_oracle(eng, trained):
+    """MT4G_OPT_LEARNED_WINDOWS: swept series scanned only at their window splits, against the
+    plain restatement of that procedure (oracle/windows_oracle.py) given the same windows and
+    confidences: change points and D bit-exact, p within 1e-12, the same fallback flags.
+    Untrained weights give poor windows: more fallbacks and answers that differ from the full
+    scan, which the procedure must still reproduce exactly."""
+    import os
+    from oracle import windows_oracle as W
+    b = synth.generate(2, 21, 40)
+    d = mt4g.to_device_samples(b.samples)
+    if trained:
+        eng.cnn_load(os.path.join(os.path.dirname(mt4g.__file__), "weights", "cnn_c2.bin"))
+    else:
+        eng.cnn_init(5)
+    win, conf = eng.propose(d, b.offsets, b.steps, 3, 16)
+    win, conf = win.cpu().numpy(), conf.cpu().numpy()
+    eng.set_option(mt4g.OPT_LEARNED_WINDOWS, 1)
+    try:
+        r = eng.ks_segment(d, b.offsets, b.steps, 1e-6, 1, 16, mode=mt4g.MODE_LEARNED)
+    finally:
+        eng.set_option(mt4g.OPT_LEARNED_WINDOWS, 0)
+    cnt, idx, num, den, p, fb = [t.cpu().numpy() for t in r[1:7]]
+    for s in range(len(b.steps)):
+        low = bool(conf[s] < np.float32(0.9))  # the threshold as the library holds it (FP32)
+        c, cps, f = W.segment_series(b.series(s), 1e-6, 1, 16, [int(c) for c in win[s]], 16, low)
+        assert (int(cnt[s]), int(fb[s])) == (c, f), s
+        for j, (k, n, dd, pp) in enumerate(cps):
+            assert (int(idx[s, j]), int(num[s, j]), int(den[s, j])) == (k, n, dd), (s, j)
+            assert abs(p[s, j] - pp) <= 1e-12 * max(pp, 1e-300), (s, j)
+
