@@ -125,18 +125,17 @@ def test_shifted_uniform_two_steps():
 
 
 def test_nested_uniform_prefix_construction():
-    """L = {1..a}, R = {1..b}, a < b (one step each side via min_seg): D = 1 - a/b."""
+    """L = {1..a}, R = {1..b}, a < b: D = max_x (x/a - x/b) = 1 - a/b at x = a.  Two steps of
+    equal size force the split: step 0 holds each of 1..a b times, step 1 each of 1..b a times
+    (the same ECDFs as L and R), so T = 2 leaves only k = 1."""
     for a in range(1, 8):
         for b in range(a + 1, 10):
-            # m = 1, steps [0, a) hold 1..a and steps [a, a+b) hold 1..b; with min_seg = a and
-            # a <= b only split a... is forced when a == b; so test the split value directly.
-            x = np.array(list(range(1, a + 1)) + list(range(1, b + 1)), np.uint32).reshape(-1, 1)
-            T = a + b
             D_direct = brute_D(list(range(1, a + 1)), list(range(1, b + 1)))
             assert D_direct == 1 - Fraction(a, b)
-            k, num, den = oracle.scan_segment(x, 0, T)
-            # the oracle's best D is at least the D of split a
-            assert Fraction(num, den) >= D_direct
+            x = np.array([np.repeat(np.arange(1, a + 1), b), np.repeat(np.arange(1, b + 1), a)], np.uint32)
+            k, num, den = oracle.scan_segment(x, 0, 2)
+            assert k == 1 and Fraction(num, den) == 1 - Fraction(a, b)
+            assert den == (a * b) * (a * b)  # n_L n_R
 
 
 # ----------------------------------------------------------------------------- invariants
