@@ -182,7 +182,7 @@ int mt4g_ks_segment(mt4g_ctx *ctx, const uint32_t *samples, const int64_t *offse
 /*
  * mt4g_ks_segment with the samples in HOST memory (the same segmentation and results).
  * The batch is cut into chunks of consecutive series of at most chunk_samples samples each
- * (<= 0: an eighth of the batch, at least 2^25; a longer series is a chunk by itself).  Chunk c + 1 is copied to the device on
+ * (<= 0: an eighth of the batch, at least 2^24; a longer series is a chunk by itself).  Chunk c + 1 is copied to the device on
  * the context's copy stream while chunk c is segmented on cuda_stream, through two device
  * staging buffers the context keeps, so the host-to-device transfer overlaps the computation;
  * give samples_host in page-locked memory (cudaMallocHost / cudaHostRegister) for the copies

@@ -1004,7 +1004,7 @@ int mt4g_ks_segment_host(mt4g_ctx *ctx, const uint32_t *samples_host, const int6
     }
     // default: about eight chunks (the first copy and the last chunk's work are not overlapped;
     // much smaller chunks leave the GPU underused), none below 2^24 samples
-    if (chunk_samples <= 0) chunk_samples = std::max<int64_t>((int64_t)1 << 25, (offsets[S] + 7) / 8);
+    if (chunk_samples <= 0) chunk_samples = std::max<int64_t>((int64_t)1 << 24, (offsets[S] + 7) / 8);
     // chunks: consecutive series up to chunk_samples samples (a larger series is a chunk alone)
     std::vector<int64_t> first{0};
     for (int64_t s = 1; s < S; s++)
