@@ -356,13 +356,32 @@ def main():
     # ---------------- end to end through host buffers (pinned), copies in the timed region
     h2d = b.samples.nbytes + b.offsets.nbytes + b.steps.nbytes
     e_steps = max(1, min(args.steps, 5))
+    # the call's chunk size (a public argument): a short trial of 2, 4, 8 and 16 chunks before the
+    # timed region picks it.  Each chunk overlaps its copy with the previous chunk's segmentation
+    # and ends on its heaviest series' critical path, so the best count depends on the batch.
+    trials = {}
+    for nch in (2, 4, 8, 16):
+        cs = (Ntot + nch - 1) // nch
+        eng.ks_segment_host(host, b.offsets, b.steps, ALPHA, 1, MAX_CP, mode=mode, stream=stream,
+                            chunk_samples=cs)
+        barrier()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        eng.ks_segment_host(host, b.offsets, b.steps, ALPHA, 1, MAX_CP, mode=mode, stream=stream,
+                            chunk_samples=cs, sync=False)
+        g1.record(stream)
+        barrier()
+        trials[nch] = max_over_ranks(g0.elapsed_time(g1))
+    e_chunks = min(trials, key=trials.get)
+    e_cs = (Ntot + e_chunks - 1) // e_chunks
     barrier()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(stream)
     outs_h = None
     for _ in range(e_steps):
         # the public host-input call: chunked host-to-device copies overlapped with segmentation
-        r = eng.ks_segment_host(host, b.offsets, b.steps, ALPHA, 1, MAX_CP, mode=mode, stream=stream, sync=False)
+        r = eng.ks_segment_host(host, b.offsets, b.steps, ALPHA, 1, MAX_CP, mode=mode, stream=stream,
+                                chunk_samples=e_cs, sync=False)
         if outs_h is None:
             outs_h = [torch.empty(x.shape, dtype=x.dtype, pin_memory=True) for x in r[1:]]
         for h_, x in zip(outs_h, r[1:]):
@@ -372,7 +391,8 @@ def main():
     te = max_over_ranks(f0.elapsed_time(f1) / 1e3)
     d2h = sum(x.numel() * x.element_size() for x in outs_h)  # every result tensor read back per step
     line["e2e"] = {"value": S * world * e_steps / te, "unit": "series/s", "h2d_bytes_per_step": int(h2d),
-                   "d2h_bytes_per_step": int(d2h), "steps": e_steps}
+                   "d2h_bytes_per_step": int(d2h), "steps": e_steps, "chunks": e_chunks,
+                   "chunk_trial_ms": {str(k): round(v, 2) for k, v in trials.items()}}
 
     # ---------------- rooflines: every stage's kernel against its bound; the dominant one is `roofline`
     peaks = {}
