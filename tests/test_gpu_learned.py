@@ -463,3 +463,39 @@ def test_window_only_scan_matches_its_oracle(eng, trained):
             assert (int(idx[s, j]), int(num[s, j]), int(den[s, j])) == (k, n, dd), (s, j)
             assert abs(p[s, j] - pp) <= 1e-12 * max(pp, 1e-300), (s, j)
 
+
+def test_window_only_ragged_shapes_and_min_seg(eng):
+    """Window-only scans on series whose rows are not 8-byte aligned (m not a multiple of 4: the
+    scalar load path), several T, and min_seg = 3, against oracle/windows_oracle.py."""
+    from oracle import windows_oracle as W
+    rng = np.random.default_rng(31)
+    series = []
+    for T, m in ((40, 6), (97, 12), (130, 40), (64, 5), (200, 24), (33, 7)):
+        lv = rng.choice([30, 80, 200], size=3)
+        cp = sorted(rng.choice(np.arange(5, T - 5), size=2, replace=False))
+        x = np.empty((T, m), np.uint32)
+        for a, bnd, l in zip([0, cp[0], cp[1]], [cp[0], cp[1], T], lv):
+            x[a:bnd] = rng.poisson(l, size=(bnd - a, m))
+        series.append(x)
+    b = synth.from_arrays(series)
+    d = mt4g.to_device_samples(b.samples)
+    eng.cnn_init(9)
+    win, conf = eng.propose(d, b.offsets, b.steps, 3, 6)
+    win, conf = win.cpu().numpy(), conf.cpu().numpy()
+    eng.set_option(mt4g.OPT_LEARNED_WINDOWS, 1)
+    eng.set_option(mt4g.OPT_HALF_WIDTH, 6)
+    eng.set_option(mt4g.OPT_CONF_MIN_PPM, 0)  # every series takes its windows
+    try:
+        r = eng.ks_segment(d, b.offsets, b.steps, 1e-6, 3, 16, mode=mt4g.MODE_LEARNED)
+    finally:
+        eng.set_option(mt4g.OPT_LEARNED_WINDOWS, 0)
+        eng.set_option(mt4g.OPT_HALF_WIDTH, 16)
+        eng.set_option(mt4g.OPT_CONF_MIN_PPM, 900000)
+    cnt, idx, num, den, p, fb = [t.cpu().numpy() for t in r[1:7]]
+    for s_, x in enumerate(series):
+        c, cps, f = W.segment_series(x, 1e-6, 3, 16, [int(c_) for c_ in win[s_]], 6, False)
+        assert (int(cnt[s_]), int(fb[s_])) == (c, f), s_
+        for j, (k, n, dd, pp) in enumerate(cps):
+            assert (int(idx[s_, j]), int(num[s_, j]), int(den[s_, j])) == (k, n, dd), (s_, j)
+            assert abs(p[s_, j] - pp) <= 1e-12 * max(pp, 1e-300), (s_, j)
+
