@@ -24,6 +24,29 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// L2 eviction priorities for the counting path (createpolicy + L2::cache_hint operands): the
+// samples are read once (evict first), the 2-byte table offsets written by the first read must
+// survive until the second pass reads them back (evict last), and the final run indices are not
+// read again by this kernel (evict first).
+__device__ __forceinline__ uint64_t pol_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t pol_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint4 ld_hint(const uint4 *a, uint64_t pol) {
+    uint4 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void st_hint(uint2 *a, uint2 v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v2.u32 [%0], {%1,%2}, %3;" ::"l"(a), "r"(v.x), "r"(v.y), "l"(pol) : "memory");
+}
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned r;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(r));
@@ -295,10 +318,14 @@ __device__ __forceinline__ void count_one(uint32_t *cnt, uint32_t v, uint32_t ba
 }
 
 // Count every sample's value - base into the table (the sort's shared memory as kFastSpan
-// counters), reading the series once with 16-byte loads; also the series' min and max.  Returns
-// false (the same in every thread) when some value fell outside the table.
+// counters), reading the series once with 16-byte loads; also the series' min and max.  Each
+// sample's table offset value - base (below kFastSpan, so 16 bits) goes to rko, in input order:
+// the run indices are later written over it in place, and while the series is being counted
+// these 2 bytes per sample stay in L2, unlike a second read of its 4-byte samples.  Returns
+// false (the same in every thread) when some value fell outside the table (rko then holds
+// nothing of use).
 __device__ bool count_values(SortSmem &sm, const uint32_t *__restrict__ in, int32_t N, uint32_t base,
-                             uint32_t &vmin, uint32_t &vmax) {
+                             uint32_t &vmin, uint32_t &vmax, uint16_t *__restrict__ rko) {
     const int tid = threadIdx.x;
     uint32_t *cnt = reinterpret_cast<uint32_t *>(&sm);
     for (uint32_t i = tid; i < kFastSpan; i += kSortThreads) cnt[i] = 0;
@@ -311,16 +338,22 @@ __device__ bool count_values(SortSmem &sm, const uint32_t *__restrict__ in, int3
         const int nt = N - vs.head - 4 * vs.nvec;
         if (tid < 32) {
             const int i = tid < vs.head ? tid : (tid - vs.head < nt ? vs.head + 4 * vs.nvec + (tid - vs.head) : -1);
-            count_one(cnt, i >= 0 ? __ldg(in + i) : 0u, base, i >= 0, out, vmin, vmax);
+            const uint32_t v = i >= 0 ? __ldg(in + i) : 0u;
+            count_one(cnt, v, base, i >= 0, out, vmin, vmax);
+            if (i >= 0) rko[i] = (uint16_t)(v - base);
         }
     }
     const uint4 *v4 = reinterpret_cast<const uint4 *>(in + vs.head);
+    // rko + head is 8-byte aligned when the samples start on a 16-byte boundary (then off + head
+    // is a multiple of 4 samples, and the label arrays are 256-byte aligned); else 2-byte stores
+    uint16_t *o = rko + vs.head;
+    const bool st8 = ((uintptr_t)o & 7u) == 0;  // the same for every thread
     for (int b0 = 0; b0 < vs.nvec; b0 += kSortThreads * kCountVec) {
         uint4 x[kCountVec];
 #pragma unroll
         for (int it = 0; it < kCountVec; it++) {
             const int i = b0 + it * kSortThreads + tid;
-            x[it] = i < vs.nvec ? __ldg(v4 + i) : make_uint4(0u, 0u, 0u, 0u);
+            x[it] = i < vs.nvec ? ld_hint(v4 + i, pol_first()) : make_uint4(0u, 0u, 0u, 0u);
         }
 #pragma unroll
         for (int it = 0; it < kCountVec; it++) {
@@ -329,6 +362,18 @@ __device__ bool count_values(SortSmem &sm, const uint32_t *__restrict__ in, int3
             count_one(cnt, x[it].y, base, valid, out, vmin, vmax);
             count_one(cnt, x[it].z, base, valid, out, vmin, vmax);
             count_one(cnt, x[it].w, base, valid, out, vmin, vmax);
+            if (valid) {
+                const int i = b0 + it * kSortThreads + tid;
+                if (st8) {
+                    st_hint(reinterpret_cast<uint2 *>(o) + i, make_uint2(((x[it].x - base) & 0xffffu) | ((x[it].y - base) << 16),
+                                                                 ((x[it].z - base) & 0xffffu) | ((x[it].w - base) << 16)), pol_last());
+                } else {
+                    o[4 * i] = (uint16_t)(x[it].x - base);
+                    o[4 * i + 1] = (uint16_t)(x[it].y - base);
+                    o[4 * i + 2] = (uint16_t)(x[it].z - base);
+                    o[4 * i + 3] = (uint16_t)(x[it].w - base);
+                }
+            }
         }
     }
     out = __syncthreads_or(out);
@@ -338,13 +383,13 @@ __device__ bool count_values(SortSmem &sm, const uint32_t *__restrict__ in, int3
 
 // Counting path, after count_values succeeded: scans the table over [vmin, vmax] for the run
 // table (starts of the distinct values in value order) and the order statistics, turns it into a
-// value -> run index table, and writes each sample's run index in input order (16-byte reads,
-// 8-byte writes where aligned).  All threads call it; returns false, with nothing written, when
-// the series has more than kSweepMaxRuns distinct values.  The sorted labels are not produced
-// (kDescNoLabels).
+// value -> run index table, and writes each sample's run index in input order over the table
+// offset count_values left there (8-byte reads and writes where aligned).  All threads call it;
+// returns false, with nothing written, when the series has more than kSweepMaxRuns distinct
+// values.  The sorted labels are not produced (kDescNoLabels).
 __device__ bool count_runs(SortSmem &sm, const uint32_t *__restrict__ in, int32_t N, uint32_t base, uint32_t vmin,
                            uint32_t vmax, int32_t *__restrict__ rt, SeriesDesc *__restrict__ ds,
-                           uint16_t *__restrict__ rko, unsigned long long *sweep_stats) {
+                           uint16_t *rko, unsigned long long *sweep_stats) {
     __shared__ uint32_t s_scan[2][kSortWarps];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint32_t *cnt = reinterpret_cast<uint32_t *>(&sm);
@@ -406,38 +451,36 @@ __device__ bool count_runs(SortSmem &sm, const uint32_t *__restrict__ in, int32_
         atomicAdd(sweep_stats + 1, (unsigned long long)N);
     }
     __syncthreads();
+    // each sample's table offset (written in input order by count_values) becomes its run
+    // index in place: coherent loads (the block wrote these words), 8 bytes = four samples
     const VecSplit vs = vec_split(in, N);
     if (tid < 32) {  // head and tail samples
         const int nt = N - vs.head - 4 * vs.nvec;
         const int i = tid < vs.head ? tid : (tid - vs.head < nt ? vs.head + 4 * vs.nvec + (tid - vs.head) : -1);
-        if (i >= 0) rko[i] = (uint16_t)cnt[__ldg(in + i) - base];
+        if (i >= 0) rko[i] = (uint16_t)cnt[rko[i]];
     }
-    const uint4 *v4 = reinterpret_cast<const uint4 *>(in + vs.head);
     uint16_t *o = rko + vs.head;
-    const bool st8 = ((uintptr_t)o & 7u) == 0;  // the same for every thread
-    for (int b0 = 0; b0 < vs.nvec; b0 += kSortThreads * kCountVec) {
-        uint4 x[kCountVec];
+    if (((uintptr_t)o & 7u) == 0) {  // the same for every thread
+        uint2 *o8 = reinterpret_cast<uint2 *>(o);
+        for (int b0 = 0; b0 < vs.nvec; b0 += kSortThreads * kCountVec) {
+            uint2 x[kCountVec];
 #pragma unroll
-        for (int it = 0; it < kCountVec; it++) {
-            const int i = b0 + it * kSortThreads + tid;
-            x[it] = i < vs.nvec ? __ldg(v4 + i) : make_uint4(base, base, base, base);
-        }
+            for (int it = 0; it < kCountVec; it++) {
+                const int i = b0 + it * kSortThreads + tid;
+                x[it] = i < vs.nvec ? o8[i] : make_uint2(0u, 0u);
+            }
 #pragma unroll
-        for (int it = 0; it < kCountVec; it++) {
-            const int i = b0 + it * kSortThreads + tid;
-            if (i < vs.nvec) {
-                const uint32_t r0 = cnt[x[it].x - base], r1 = cnt[x[it].y - base];
-                const uint32_t r2 = cnt[x[it].z - base], r3 = cnt[x[it].w - base];
-                if (st8) {
-                    reinterpret_cast<uint2 *>(o)[i] = make_uint2(r0 | (r1 << 16), r2 | (r3 << 16));
-                } else {
-                    o[4 * i] = (uint16_t)r0;
-                    o[4 * i + 1] = (uint16_t)r1;
-                    o[4 * i + 2] = (uint16_t)r2;
-                    o[4 * i + 3] = (uint16_t)r3;
+            for (int it = 0; it < kCountVec; it++) {
+                const int i = b0 + it * kSortThreads + tid;
+                if (i < vs.nvec) {
+                    const uint32_t r0 = cnt[x[it].x & 0xffffu], r1 = cnt[x[it].x >> 16];
+                    const uint32_t r2 = cnt[x[it].y & 0xffffu], r3 = cnt[x[it].y >> 16];
+                    st_hint(o8 + i, make_uint2(r0 | (r1 << 16), r2 | (r3 << 16)), pol_first());
                 }
             }
         }
+    } else {
+        for (int i = tid; i < 4 * vs.nvec; i += kSortThreads) o[i] = (uint16_t)cnt[o[i]];
     }
     return true;
 }
@@ -511,10 +554,10 @@ sort_series_kernel(const uint32_t *__restrict__ samples, SeriesDesc *__restrict_
         const uint32_t v0 = __ldg(in);
         // the table [base, base + kFastSpan) must not wrap past 2^32 - 1
         uint32_t base = min(v0 - min(v0, kBaseBelow), 0xffffffffu - kFastSpan + 1u);
-        bool ok = count_values(sm, in, N, base, vmin, vmax);
+        bool ok = count_values(sm, in, N, base, vmin, vmax, labB + off);
         if (!ok && vmax - vmin < kFastSpan) {
             base = vmin;
-            ok = count_values(sm, in, N, base, vmin, vmax);
+            ok = count_values(sm, in, N, base, vmin, vmax, labB + off);
         }
         if (ok && count_runs(sm, in, N, base, vmin, vmax, rt, desc + s, labB + off, sweep_stats)) return;
         // too many distinct values (or too wide a span) for the counting path: radix sort

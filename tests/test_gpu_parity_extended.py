@@ -282,3 +282,24 @@ def test_many_distinct_values_match_oracle(eng):
             assert _close(sc[3], oscan[3], P_RTOL)
     finally:
         eng.set_option(mt4g.OPT_SCAN_KPT, 0)
+
+
+def test_samples_pointer_off_a_16_byte_boundary(eng):
+    """The counting sort writes each sample's table offset and then its run index with 8-byte
+    accesses where the run-index array lines up with the samples' 16-byte boundary; a samples
+    pointer one element past an allocation's start takes the 2-byte path instead.  Both give the
+    oracle's segmentation."""
+    import torch
+    b = synth.generate(2, 12, 24)
+    n = int(b.offsets[-1])
+    buf = torch.empty(n + 1, dtype=torch.int32, device="cuda")
+    buf[1:] = torch.from_numpy(b.samples.view(np.int32)).cuda()
+    _, ocnt, oidx, onum, oden, op = oracle.ks_segment(b.samples, b.offsets, b.steps, 1e-6, 1, 16, nthreads=8)
+    for view in (buf[1:], torch.from_numpy(b.samples.view(np.int32)).cuda()):
+        r = eng.ks_segment(view, b.offsets, b.steps, 1e-6, 1, 16)
+        got = [t.cpu().numpy() for t in r[1:6]]
+        for a, c in zip([ocnt, oidx, onum, oden], got[:4]):
+            assert np.array_equal(a, c)
+        assert (np.abs(got[4] - op) <= 1e-12 * np.abs(op)).all()
+        assert eng.last_sweep()["counted_samples"] == n  # the counting path took every series
+
