@@ -61,7 +61,7 @@ RECIPES = {2: "synth recipe 2 (T=512, m=128, levels 35/300/800/1100, 0.5% outlie
 # The queue kernels: profiles/queue_kernel_learned_sweep_4096x512x128.md and
 # profiles/queue_kernel_sweep_4096x512x128.md (4096 series each).
 NCU_TRAFFIC_PER_SERIES = {("plain", "sort"): 1646.202e6 / 4096, ("learned", "sort"): 1646.202e6 / 4096,
-                          ("learned", "queue"): 2416.624e6 / 4096, ("plain", "queue"): 2388.549e6 / 4096}
+                          ("learned", "queue"): 2426.104e6 / 4096, ("plain", "queue"): 2392.948e6 / 4096}
 STAGES = ["upload", "sort", "proposals", "queue", "collect"]
 
 

@@ -724,21 +724,21 @@ __device__ void sweep_move_range(SweepStage &ss, const uint16_t *__restrict__ rk
 }
 
 // Four runs of a lane's block: running l sum hc, values hc - a C relative to the run before
-// the block, their max and min (three-input integer max / min).
+// the block, their max and min (two-input max / min: the three-input intrinsics ran slower).
 __device__ __forceinline__ void sweep_eval4(const uint4 q, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                                             uint32_t na, uint32_t &hc, int32_t &mx, int32_t &mn) {
     hc += q.x;
     const int32_t v0 = (int32_t)(hc + na * c0);
     hc += q.y;
     const int32_t v1 = (int32_t)(hc + na * c1);
-    mx = __vimax3_s32(mx, v0, v1);
-    mn = __vimin3_s32(mn, v0, v1);
+    mx = max(mx, max(v0, v1));
+    mn = min(mn, min(v0, v1));
     hc += q.z;
     const int32_t v2 = (int32_t)(hc + na * c2);
     hc += q.w;
     const int32_t v3 = (int32_t)(hc + na * c3);
-    mx = __vimax3_s32(mx, v2, v3);
-    mn = __vimin3_s32(mn, v2, v3);
+    mx = max(mx, max(v2, v3));
+    mn = min(mn, min(v2, v3));
 }
 
 // Best split (k, g) over A <= k <= B of segment [lo, hi) of a run-sweep series (A > lo: the
