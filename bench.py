@@ -94,7 +94,12 @@ def workload_config(name, world, S):
 # ----------------------------------------------------------------------------- clocks
 
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi sampling the SM clock and throttle reasons while a timed region runs.
+
+    Any NVML client attached to the GPU (this sampler, an idle nvidia-smi, or one NVML handle in
+    the process) slows the segmentation by about 2.3% on B300, whatever it queries and however
+    often, so every device-timed arm that a ratio compares runs with a sampler of its own."""
+    FIELDS =("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -298,7 +303,7 @@ def main():
         eng.cnn_load(WEIGHTS)
         res_p = [x.clone() for x in out_main[1:6]]
         graph = False
-        t_l, out_l, _, stages_l, evals_l, _ = timed(mt4g.MODE_LEARNED, args.steps, 1)
+        t_l, out_l, _, stages_l, evals_l, clk_l = timed(mt4g.MODE_LEARNED, args.steps, 1, ClockSampler(local))
         st_l = eng.learned_stats()
         same_l = torch.ones(S, dtype=torch.bool, device=dev)
         for a_, c_ in zip(res_p, out_l[1:6]):
@@ -307,19 +312,19 @@ def main():
                            "speedup_vs_plain": t_main / t_l, "agreement": float(same_l.float().mean().item()),
                            "fallback_rate": float(out_l[6].float().mean().item()), "evals": evals_l,
                            "evals_plain": evals, "certified_segments": st_l["certified"],
-                           "refined_segments": st_l["refined"],
+                           "refined_segments": st_l["refined"], "clocks": clk_l,
                            "stage_ms": dict(zip(STAGES, np.asarray(stages_l).mean(axis=0).tolist()))}
     if learned:
         res_l = [x.clone() for x in out_main[1:6]]
         fb = out_main[6].clone()
-        t_plain, out_plain, _, stages_p, evals_p, _ = timed(mt4g.MODE_FULL, args.steps, 1)
+        t_plain, out_plain, _, stages_p, evals_p, clk_p = timed(mt4g.MODE_FULL, args.steps, 1, ClockSampler(local))
         same = torch.ones(S, dtype=torch.bool, device=dev)
         for a, c in zip(res_l, out_plain[1:6]):
             same &= (a == c).reshape(S, -1).all(dim=1)
         plain_value = S * world * args.steps / t_plain
         eng.set_option(mt4g.OPT_SCAN_KPT, 1)  # the probe path on slices, for comparison
         try:
-            t_sl, out_sl, _, stages_sl, evals_sl, _ = timed(mode, args.steps, 1)
+            t_sl, out_sl, _, stages_sl, evals_sl, clk_sl = timed(mode, args.steps, 1, ClockSampler(local))
             stats_sl = eng.learned_stats()
             same_sl = torch.ones(S, dtype=torch.bool, device=dev)
             for a, c in zip(res_l, out_sl[1:6]):
@@ -330,12 +335,12 @@ def main():
             "value": S * world * args.steps / t_sl, "ms_per_step": t_sl / args.steps * 1e3,
             "agreement": float(same_sl.float().mean().item()), "evals": evals_sl,
             "certified_segments": stats_sl["certified"], "refined_segments": stats_sl["refined"],
-            "stage_ms": dict(zip(STAGES, np.asarray(stages_sl).mean(axis=0).tolist()))}
+            "clocks": clk_sl, "stage_ms": dict(zip(STAGES, np.asarray(stages_sl).mean(axis=0).tolist()))}
         # window-only scans of the swept series (no certification): agreement with the full
         # scan measured per series, low-confidence and non-significant series fall back
         eng.set_option(mt4g.OPT_LEARNED_WINDOWS, 1)
         try:
-            t_w, out_w, _, stages_w, evals_w, _ = timed(mode, args.steps, 1)
+            t_w, out_w, _, stages_w, evals_w, clk_w = timed(mode, args.steps, 1, ClockSampler(local))
         finally:
             eng.set_option(mt4g.OPT_LEARNED_WINDOWS, 0)
         same_w = torch.ones(S, dtype=torch.bool, device=dev)
@@ -344,13 +349,13 @@ def main():
         line["learned_windows"] = {
             "value": S * world * args.steps / t_w, "ms_per_step": t_w / args.steps * 1e3,
             "speedup_vs_plain": t_plain / t_w, "agreement": float(same_w.float().mean().item()),
-            "fallback_rate": float(out_w[6].float().mean().item()), "evals": evals_w,
+            "fallback_rate": float(out_w[6].float().mean().item()), "evals": evals_w, "clocks": clk_w,
             "stage_ms": dict(zip(STAGES, np.asarray(stages_w).mean(axis=0).tolist()))}
         line.update({"plain_value": plain_value, "plain_ms_per_step": t_plain / args.steps * 1e3,
                      "speedup_vs_plain": value / plain_value, "agreement": float(same.float().mean().item()),
                      "fallback_rate": float(fb.float().mean().item()),
                      "certified_segments": stats["certified"], "refined_segments": stats["refined"],
-                     "evals_learned": evals, "evals_plain": evals_p,
+                     "evals_learned": evals, "evals_plain": evals_p, "plain_clocks": clk_p,
                      "plain_stage_ms": dict(zip(STAGES, np.asarray(stages_p).mean(axis=0).tolist()))})
 
     # ---------------- end to end through host buffers (pinned), copies in the timed region

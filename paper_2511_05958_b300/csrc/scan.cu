@@ -579,8 +579,8 @@ __device__ __forceinline__ void warp_best(int &bk, uint64_t &bg, int lo, int hi)
 // update costs O(m), and the values at all runs follow from one pass over l.
 //
 // Lane L owns the block of R consecutive runs [L R, L R + R), R = ceil(U' / 32) rounded up to
-// a multiple of 4, so that every lane walks the same number of runs and needs no per-run
-// bounds test; positions at or past U' hold l = 0 and C = N (= m H), which repeat the value
+// a multiple of 8, so that every lane walks the same number of runs in pairs of 16-byte loads
+// and needs no per-run or per-load bounds test; positions at or past U' hold l = 0 and C = N (= m H), which repeat the value
 // at the last run, v_k(U' - 1) = H m a - a m H = 0.  Within the block the lane accumulates
 // the values relative to the run before the block,
 //     v_k(c) - v_k(L R - 1) = sum_{L R <= c' <= c} l_k(c') - a (C_c - C_{L R - 1}),
@@ -590,17 +590,19 @@ __device__ __forceinline__ void warp_best(int &bk, uint64_t &bg, int lo, int hi)
 // g_k.  The sweep takes segments with m H^2 < 2^31, where every quantity above is an exact
 // 32-bit integer.
 //
-// Layout: the l of lane L's block sits at words [L Rs, L Rs + R) of the stage, Rs = R when
-// R = 4 mod 8 and R + 4 otherwise; a lane reads its block four runs at a time (16-byte
-// loads), and with Rs = 4 mod 8 the eight lanes of a quarter warp start on eight different
+// Layout: the l of lane L's block sits at words [L Rs, L Rs + R) of the stage, Rs = R + 4; a
+// lane reads its block four runs at a time (16-byte loads), and with Rs = 4 mod 8 the eight lanes of a quarter warp start on eight different
 // four-bank groups, so the loads are free of bank conflicts.  Each lane keeps its block's C
 // in registers (they do not change during a segment's sweep).
-constexpr int kSweepMaxR = 48;                       // ceil(kSweepMaxRuns / 32), a multiple of 4
+constexpr int kSweepMaxR = 48;                       // ceil(kSweepMaxRuns / 32), a multiple of 8
 constexpr int kSweepLWords = 32 * (kSweepMaxR + 4);  // largest padded layout
+// The evaluation loads a lane's next two quads before it knows whether its block has them: the
+// last lane reads up to 4 words past the layout, into this tail (values never used).
+constexpr int kSweepLTail = 16;
 static_assert(kSweepMaxRuns <= 32 * kSweepMaxR && kSweepMaxR % 8 == 0, "lane blocks of kSweepMaxR runs");
 
 struct __align__(16) SweepStage {
-    uint32_t l[kSweepLWords];     // setup: count of series run r, then C of compact run c; sweep: l by layout position
+    uint32_t l[kSweepLWords + kSweepLTail];  // setup: count of series run r, then C of compact run c; sweep: l by layout position
     uint16_t map[kSweepMaxRuns];  // series run -> layout position of its compact run
 };
 
@@ -881,8 +883,8 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
     const uint32_t N = cs;  // m H
     nonempty = Uc;
     int R = (Uc + 31) >> 5;
-    R = max(4, (R + 3) & ~3);
-    const int Rs = (R & 7) ? R : R + 4;
+    R = max(8, (R + 7) & ~7);
+    const int Rs = R + 4;
     const int nq = R >> 2;  // quads per block
     const int b0 = lane * R;
     const uint32_t Cb = b0 == 0 ? 0u : (b0 <= Uc ? ss.l[b0 - 1] : N);  // in-segment samples below the block
@@ -938,26 +940,22 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
             kb = kp + 1;
         }
     };
-    const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
     // the values of split k into p_blk, p_h0, p_mx, p_mn (l holds the left counts of split k)
     auto evaluate = [&](int k) {
         const uint32_t a = (uint32_t)(k - lo), na = 0u - a;
         const uint32_t h0 = a * Cb;
         uint32_t hc = h0;
         int32_t mx = INT_MIN, mn = INT_MAX;
-        uint4 q0 = lq[0], q1 = zero4;
-        if (nq > 1) q1 = lq[1];
-        // the block in groups of two quads, the next group's loads issued before the current
-        // group is evaluated; nq is the same for every lane
+        uint4 q0 = lq[0], q1 = lq[1];
+        // the block in groups of two quads (nq is even), the next group's loads issued before the
+        // current group is evaluated, whether or not the block has them (nq is the same for every
+        // lane; the two quads after the block's last are loaded, within the stage, and not used)
 #pragma unroll
         for (int g = 0; g < kSweepMaxR / 8; g++) {
             if (2 * g >= nq) break;
-            uint4 n0 = zero4, n1 = zero4;
-            if (2 * g + 2 < nq) n0 = lq[2 * g + 2];
-            if (2 * g + 3 < nq) n1 = lq[2 * g + 3];
+            const uint4 n0 = lq[2 * g + 2], n1 = lq[2 * g + 3];
             sweep_eval4(q0, Cr[8 * g], Cr[8 * g + 1], Cr[8 * g + 2], Cr[8 * g + 3], na, hc, mx, mn);
-            if (2 * g + 1 < nq)
-                sweep_eval4(q1, Cr[8 * g + 4], Cr[8 * g + 5], Cr[8 * g + 6], Cr[8 * g + 7], na, hc, mx, mn);
+            sweep_eval4(q1, Cr[8 * g + 4], Cr[8 * g + 5], Cr[8 * g + 6], Cr[8 * g + 7], na, hc, mx, mn);
             q0 = n0;
             q1 = n1;
         }
@@ -1012,13 +1010,14 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
         }
     }
     // every split of [Ai, Bi] in order, software-pipelined: run indices two steps ahead, split
-    // k - 1 finished while split k's first loads are in flight; step k moves left after split k
-    // for k < Bi (step Bi stays on the right)
+    // k - 1 finished while split k's first loads are in flight; step k moves left after split k,
+    // step Bi too (nothing reads l after the last split but the window walk, which goes on from
+    // step Bi + 1), so that the loop has no per-split tests
     auto sweep_range = [&](int Ai, int Bi) {
         kb = Ai;
         StepBuf<VEC> nxt, nxt2;
         sweep_load_step<VEC>(rk, Ai, m, lane, nxt);
-        if (Ai + 1 <= Bi) sweep_load_step<VEC>(rk, Ai + 1, m, lane, nxt2);
+        sweep_load_step<VEC>(rk, min(Ai + 1, Bi), m, lane, nxt2);
         for (int k = Ai; k <= Bi; k++) {
             const StepBuf<VEC> cur = nxt;
             uint32_t pos0 = 0, pos1 = 0, pos2 = 0, pos3 = 0;
@@ -1029,7 +1028,7 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
                 pos3 = ss.map[cur.v[1] >> 16];
             }
             nxt = nxt2;
-            if (k + 2 <= Bi) sweep_load_step<VEC>(rk, k + 2, m, lane, nxt2);
+            sweep_load_step<VEC>(rk, min(k + 2, Bi), m, lane, nxt2);  // past Bi: a step of the segment, unused
             __syncwarp();
             if (k > Ai) finish(k - 1, Bi);
             nev++;
@@ -1037,7 +1036,7 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
             // every lane has read l for split k: step k's samples move left now (reductions the warp
             // does not wait for)
             __syncwarp();
-            if (k < Bi) {
+            {
                 if constexpr (VEC) {
                     if (4 * lane < m) {
                         atomicAdd(&ss.l[pos0], H);
@@ -1070,7 +1069,7 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
         while (window_interval(P, series, from, B, a, b)) {
             if (prev >= 0) {
                 __syncwarp();
-                sweep_move_range<VEC>(ss, rk, prev, a, m, H, lane);  // steps prev .. a - 1
+                sweep_move_range<VEC>(ss, rk, prev + 1, a, m, H, lane);  // steps prev + 1 .. a - 1
             }
             sweep_range(a, b);
             prev = b;

@@ -4,10 +4,10 @@ The CUDA kernels cannot run here; these tests replay, in plain Python integers r
 the way the kernels' registers wrap, the formulation the kernels use, and compare it with the
 definition g_k = max_x |H c_L(x) - a C(x)| (Sec. II-C-1, Sec. IV-B-1 (4)) evaluated by brute force.
 What is pinned:
-  - the per-lane blocks of runs: R = ceil(U'/32) rounded up to a multiple of 4 (at least 4), the
+  - the per-lane blocks of runs: R = ceil(U'/32) rounded up to a multiple of 8 (at least 8), the
     same for all 32 lanes, positions at or past U' padded with l = 0 and C = N,
-  - the padded layout (lane stride R or R + 4 words) and the run -> layout position map, within
-    the stage's 32 (48 + 4) words,
+  - the padded layout (lane stride R + 4 words) and the run -> layout position map, within
+    the stage's 32 (48 + 4) words, and the evaluation's loads two quads ahead within its tail,
   - values accumulated relative to the run before each block, four runs per 16-byte load, with the
     block's offset taken from a scan of the blocks' sums of l afterwards,
   - the counting sort's run table, run indices and nearest-rank order statistics.
@@ -36,13 +36,13 @@ def brute_g(x, m, lo, hi):
     return out
 
 
-MAX_R, STAGE_WORDS = 48, 32 * (48 + 4)
+MAX_R, STAGE_WORDS, STAGE_TAIL = 48, 32 * (48 + 4), 16
 
 
 def lane_blocks(Uc):
     """Block size R, lane stride Rs and each lane's first run."""
-    R = max(4, -(-((Uc + 31) // 32) // 4) * 4)
-    Rs = R if R % 8 == 4 else R + 4
+    R = max(8, -(-((Uc + 31) // 32) // 8) * 8)
+    Rs = R + 4
     return R, Rs, [L * R for L in range(32)]
 
 
@@ -119,12 +119,17 @@ def test_sweep_arithmetic_matches_definition(seed):
 
 def test_lane_blocks_cover_every_size():
     """For every U' up to the sweep's 1536 runs: 32 blocks of R runs cover [0, U'), R <= 48 is a
-    multiple of 4, the layout fits the stage, and the eight lanes of a quarter warp start their
-    16-byte loads on eight different four-bank groups (lane stride Rs = 4 mod 8)."""
+    multiple of 8, the layout fits the stage, the evaluation's loads (groups of two quads, the next
+    group loaded before the current one is evaluated) stay within the stage and its tail, and the
+    eight lanes of a quarter warp start their 16-byte loads on eight different four-bank groups
+    (lane stride Rs = 4 mod 8)."""
     for Uc in range(1, 1537):
         R, Rs, firsts = lane_blocks(Uc)
-        assert R % 4 == 0 and 4 <= R <= MAX_R and 32 * R >= Uc and 32 * Rs <= STAGE_WORDS
-        assert R == 4 or 32 * (R - 4) < Uc  # no larger than needed
+        assert R % 8 == 0 and 8 <= R <= MAX_R and 32 * R >= Uc and 32 * Rs <= STAGE_WORDS
+        assert R == 8 or 32 * (R - 8) < Uc  # no larger than needed
+        nq = R // 4
+        last_quad = max(2 * g + 3 for g in range(nq // 2))  # quads 0 and 1 first, then 2g+2, 2g+3
+        assert 31 * Rs + 4 * last_quad + 3 < STAGE_WORDS + STAGE_TAIL
         assert Rs % 8 == 4
         for q in range(R // 4):
             for L0 in range(0, 32, 8):
