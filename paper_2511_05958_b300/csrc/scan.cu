@@ -855,27 +855,45 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
         }
     }
     __syncwarp();
-    // compaction, 32 runs per round: a run's compact slot is never above its own index, and
-    // every round reads its counts before it writes, so the later rounds' counts survive.
-    // Absent runs keep a stale map entry; no sample of the segment refers to them.
+    // compaction, 128 runs per round (four consecutive runs per lane, one 16-byte load): a run's
+    // compact slot is never above its own index, and every round reads its counts before it
+    // writes, so the later rounds' counts survive.  Absent runs keep a stale map entry; no
+    // sample of the segment refers to them.
     uint32_t nc = 0, cs = 0;  // runs kept so far, in-segment samples so far
-    for (int r0 = 0; r0 < U; r0 += 32) {
-        const int r = r0 + lane;
-        const uint32_t n = r < U ? ss.l[r] : 0u;
-        const unsigned keep = __ballot_sync(kFull, n != 0);
-        uint32_t incl = n;
+    for (int r0 = 0; r0 < U; r0 += 128) {
+        const int rb = r0 + 4 * lane;
+        const uint4 q = *reinterpret_cast<const uint4 *>(&ss.l[rb]);  // within the stage (U <= 1536)
+        const uint32_t n0 = rb < U ? q.x : 0u, n1 = rb + 1 < U ? q.y : 0u;
+        const uint32_t n2 = rb + 2 < U ? q.z : 0u, n3 = rb + 3 < U ? q.w : 0u;
+        const uint32_t s1 = n0 + n1, s2 = s1 + n2, s3 = s2 + n3;
+        const unsigned k0 = __ballot_sync(kFull, n0 != 0), k1 = __ballot_sync(kFull, n1 != 0);
+        const unsigned k2 = __ballot_sync(kFull, n2 != 0), k3 = __ballot_sync(kFull, n3 != 0);
+        uint32_t incl = s3;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(kFull, incl, o);
             if (lane >= o) incl += y;
         }
         __syncwarp();
-        if (n != 0) {
-            const uint32_t ci = nc + (uint32_t)__popc(keep & lt);
-            ss.map[r] = (uint16_t)ci;
-            ss.l[ci] = cs + incl;  // C of compact run ci, until the lanes have read it
+        const uint32_t below = cs + incl - s3;  // in-segment samples of the runs before rb
+        uint32_t ci = nc + (uint32_t)(__popc(k0 & lt) + __popc(k1 & lt) + __popc(k2 & lt) + __popc(k3 & lt));
+        if (n0 != 0) {
+            ss.map[rb] = (uint16_t)ci;
+            ss.l[ci++] = below + n0;  // C of compact run ci, until the lanes have read it
         }
-        nc += (uint32_t)__popc(keep);
+        if (n1 != 0) {
+            ss.map[rb + 1] = (uint16_t)ci;
+            ss.l[ci++] = below + s1;
+        }
+        if (n2 != 0) {
+            ss.map[rb + 2] = (uint16_t)ci;
+            ss.l[ci++] = below + s2;
+        }
+        if (n3 != 0) {
+            ss.map[rb + 3] = (uint16_t)ci;
+            ss.l[ci] = below + s3;
+        }
+        nc += (uint32_t)(__popc(k0) + __popc(k1) + __popc(k2) + __popc(k3));
         cs += __shfl_sync(kFull, incl, 31);
         __syncwarp();
     }
@@ -890,14 +908,22 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
     const uint32_t Cb = b0 == 0 ? 0u : (b0 <= Uc ? ss.l[b0 - 1] : N);  // in-segment samples below the block
     uint32_t Cr[kSweepMaxR];
 #pragma unroll
-    for (int j = 0; j < kSweepMaxR; j++) Cr[j] = (j < R && b0 + j < Uc) ? ss.l[b0 + j] : N;
+    for (int i = 0; i < kSweepMaxR / 4; i++) {  // 16-byte loads (b0 is a multiple of 8), within the stage
+        const uint4 q = *reinterpret_cast<const uint4 *>(&ss.l[b0 + 4 * i]);
+        Cr[4 * i] = b0 + 4 * i < Uc ? q.x : N;  // registers past R are never read
+        Cr[4 * i + 1] = b0 + 4 * i + 1 < Uc ? q.y : N;
+        Cr[4 * i + 2] = b0 + 4 * i + 2 < Uc ? q.z : N;
+        Cr[4 * i + 3] = b0 + 4 * i + 3 < Uc ? q.w : N;
+    }
     __syncwarp();
-    // compact index -> layout position, then l = 0 over the whole layout
+    // compact index -> layout position ci + 4 floor(ci / R); with R = 8 d (d <= 6) and
+    // ci < 1536, floor(ci / R) = ((ci >> 3) (2^16 / d + 1)) >> 16 exactly
+    const uint32_t magic = 65536u / (uint32_t)(R >> 3) + 1u;
     for (int r = lane; r < U; r += 32) {
         const uint32_t ci = ss.map[r];
-        ss.map[r] = (uint16_t)((ci / (uint32_t)R) * (uint32_t)Rs + ci % (uint32_t)R);
+        ss.map[r] = (uint16_t)(ci + 4u * (((ci >> 3) * magic) >> 16));
     }
-    for (int w = lane; w < 32 * Rs; w += 32) ss.l[w] = 0u;
+    for (int w = 4 * lane; w < 32 * Rs; w += 128) *reinterpret_cast<uint4 *>(&ss.l[w]) = make_uint4(0u, 0u, 0u, 0u);
     __syncwarp();
 
     sweep_move_range<VEC>(ss, rk, lo, A, m, H, lane);
@@ -923,7 +949,7 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
         }
         const uint32_t vs = (incl - p_blk) - p_h0;  // v at the run before the block
         const int32_t bmax = (int32_t)(vs + (uint32_t)p_mx), bmin = (int32_t)(vs + (uint32_t)p_mn);
-        const uint32_t gl = max((uint32_t)max(bmax, 0), (uint32_t)max(-bmin, 0));
+        const uint32_t gl = (uint32_t)max(bmax, -bmin);  // max |v| over the block (bmin <= bmax)
         return __reduce_max_sync(kFull, gl);
     };
     // without skipping the argmax is taken 32 splits at a time (lane j holds split kb + j);
@@ -1021,7 +1047,7 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
         for (int k = Ai; k <= Bi; k++) {
             const StepBuf<VEC> cur = nxt;
             uint32_t pos0 = 0, pos1 = 0, pos2 = 0, pos3 = 0;
-            if (VEC && 4 * lane < m) {
+            if (VEC) {  // lanes past the step's m samples look up run 0 and do not use it
                 pos0 = ss.map[cur.v[0] & 0xffffu];
                 pos1 = ss.map[cur.v[0] >> 16];
                 pos2 = ss.map[cur.v[1] & 0xffffu];
@@ -1030,7 +1056,7 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
             nxt = nxt2;
             sweep_load_step<VEC>(rk, min(k + 2, Bi), m, lane, nxt2);  // past Bi: a step of the segment, unused
             __syncwarp();
-            if (k > Ai) finish(k - 1, Bi);
+            finish(k - 1, Bi);  // at k = Ai it records nothing (no lane has split kb - 1)
             nev++;
             evaluate(k);
             // every lane has read l for split k: step k's samples move left now (reductions the warp

@@ -127,6 +127,8 @@ def test_lane_blocks_cover_every_size():
         R, Rs, firsts = lane_blocks(Uc)
         assert R % 8 == 0 and 8 <= R <= MAX_R and 32 * R >= Uc and 32 * Rs <= STAGE_WORDS
         assert R == 8 or 32 * (R - 8) < Uc  # no larger than needed
+        magic = 65536 // (R // 8) + 1  # the kernel's layout position ci + 4 floor(ci / R)
+        assert all(ci + 4 * (((ci >> 3) * magic) >> 16) == (ci // R) * Rs + ci % R for ci in range(Uc))
         nq = R // 4
         last_quad = max(2 * g + 3 for g in range(nq // 2))  # quads 0 and 1 first, then 2g+2, 2g+3
         assert 31 * Rs + 4 * last_quad + 3 < STAGE_WORDS + STAGE_TAIL
