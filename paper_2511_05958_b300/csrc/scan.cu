@@ -755,7 +755,7 @@ constexpr int kWalkAll = 0, kWalkSkip = 1, kWalkWindows = 2;
 // kWalkSkip: exact bound skipping.  Moving one step's m samples changes every v(c) by H s(c) - C(c),
 // s(c) <= m and C(c) <= m H, so |g_{k+j} - g_k| <= j m H.  A split whose bound from the last
 // evaluated split e, g_e + (k - e) m H, gives a D strictly below the best D found so far,
-//     (g_e + (k - e) m H) a_b (H - a_b) < g_b a_k (H - a_k)        (128-bit products),
+//     (g_e + (k - e) m H) a_b (H - a_b) < g_b a_k (H - a_k)        (64-bit products: m H^2 < 2^31),
 // can be neither the argmax nor tie with it, so it is not evaluated; its samples still move.
 // Window-only learned scan (MT4G_OPT_LEARNED_WINDOWS): split k of series `series` is a
 // candidate when |k - c| <= half for one of its window centres c (c < 0: no window).
@@ -992,48 +992,83 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
     };
     nev = 0;
     if constexpr (WALK == kWalkSkip) {
-        {
-        // Walk: evaluate split k; the bound from it, with the best so far, excludes a run of the
-        // following splits (lane i tests split k + 1 + i, a ballot gives the run's length); the
-        // steps up to the next split to evaluate move left in one pass, with no per-split work.
-        int k = A;
-        StepBuf<VEC> cur;
-        sweep_load_step<VEC>(rk, A, m, lane, cur);
-        while (k <= B) {
-            __syncwarp();
-            evaluate(k);
-            const uint32_t g = split_g();
-            nev++;
-            if (better(k, (uint64_t)g, bk, bg, lo, hi)) {
-                bk = k;
-                bg = g;
+        // Exact bound skipping, pipelined like the full walk (run indices two steps ahead, every
+        // step's samples moved after its split): split k is evaluated only when the bound from the
+        // last evaluated split e, g_e + (k - e) m H, can reach the best D so far.  With
+        // m H^2 < 2^31 both products of the test stay below 2^61.
+        int e = kNoK;
+        uint32_t ge = 0;
+        bool pending = false;  // split e evaluated, its g not yet taken
+        StepBuf<VEC> nxt, nxt2;
+        sweep_load_step<VEC>(rk, A, m, lane, nxt);
+        sweep_load_step<VEC>(rk, min(A + 1, B), m, lane, nxt2);
+        const uint64_t mH = (uint64_t)m * H;
+        for (int k = A; k <= B; k++) {
+            const StepBuf<VEC> cur = nxt;
+            uint32_t pos0 = 0, pos1 = 0, pos2 = 0, pos3 = 0;
+            if (VEC) {  // lanes past the step's m samples look up run 0 and do not use it
+                pos0 = ss.map[cur.v[0] & 0xffffu];
+                pos1 = ss.map[cur.v[0] >> 16];
+                pos2 = ss.map[cur.v[1] & 0xffffu];
+                pos3 = ss.map[cur.v[1] >> 16];
             }
-            const uint64_t db = (uint64_t)(bk - lo) * (uint64_t)(hi - bk);
-            int next = k + 1;
-            for (;;) {
-                const int kk = next + lane;
-                bool skip = false;
-                if (kk <= B) {
-                    const uint64_t ub = (uint64_t)g + (uint64_t)(kk - k) * (uint64_t)m * (uint64_t)H;
-                    const uint64_t dk = (uint64_t)(kk - lo) * (uint64_t)(hi - kk);
-                    skip = prod_less(ub, db, bg, dk);
+            nxt = nxt2;
+            sweep_load_step<VEC>(rk, min(k + 2, B), m, lane, nxt2);
+            if (pending) {
+                ge = split_g();
+                if (better(e, (uint64_t)ge, bk, bg, lo, hi)) {
+                    bk = e;
+                    bg = ge;
                 }
-                const unsigned sm = __ballot_sync(kFull, skip);
-                const int run = sm == kFull ? 32 : __ffs(~sm) - 1;
-                next += run;
-                if (run < 32) break;
+                pending = false;
             }
-            if (next > B) break;  // every remaining split is excluded
-            // every lane has read l for split k: steps k .. next - 1 move left
-            __syncwarp();
-            sweep_apply_step<VEC>(ss, rk, k, m, H, lane, cur);  // step k, loaded during split k
-            sweep_move_range<VEC>(ss, rk, k + 1, next, m, H, lane);
-            k = next;
-            if (k <= B) sweep_load_step<VEC>(rk, k, m, lane, cur);
+            bool ev = true;
+            if (e != kNoK) {
+                const uint64_t ub = (uint64_t)ge + (uint64_t)(k - e) * mH;
+                const uint64_t db = (uint64_t)(bk - lo) * (uint64_t)(hi - bk);
+                const uint64_t dk = (uint64_t)(k - lo) * (uint64_t)(hi - k);
+                ev = !(ub * db < (uint64_t)bg * dk);
+            }
+            // the barriers order the moves only around an evaluation: the moves of skipped splits
+            // follow one another with none
+            if (ev) {
+                __syncwarp();
+                nev++;
+                evaluate(k);
+                e = k;
+                pending = true;
+                __syncwarp();
+            }
+            if constexpr (VEC) {
+                if (4 * lane < m) {
+                    atomicAdd(&ss.l[pos0], H);
+                    atomicAdd(&ss.l[pos1], H);
+                    atomicAdd(&ss.l[pos2], H);
+                    atomicAdd(&ss.l[pos3], H);
+                }
+                const uint16_t *src = rk + (int64_t)k * m;
+                for (int j0 = 128; j0 < m; j0 += 128) {
+                    const bool a2 = j0 + 4 * lane < m;
+                    uint2 x = make_uint2(0u, 0u);
+                    if (a2) x = __ldg(reinterpret_cast<const uint2 *>(src + j0) + lane);
+                    lc_add(ss, x.x & 0xffffu, H, a2);
+                    lc_add(ss, x.x >> 16, H, a2);
+                    lc_add(ss, x.y & 0xffffu, H, a2);
+                    lc_add(ss, x.y >> 16, H, a2);
+                }
+            } else {
+                sweep_apply_step<VEC>(ss, rk, k, m, H, lane, cur);
+            }
+        }
+        if (pending) {
+            ge = split_g();
+            if (better(e, (uint64_t)ge, bk, bg, lo, hi)) {
+                bk = e;
+                bg = ge;
+            }
         }
         __syncwarp();
         return;
-        }
     }
     // every split of [Ai, Bi] in order, software-pipelined: run indices two steps ahead, split
     // k - 1 finished while split k's first loads are in flight; step k moves left after split k,
