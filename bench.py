@@ -61,7 +61,7 @@ RECIPES = {2: "synth recipe 2 (T=512, m=128, levels 35/300/800/1100, 0.5% outlie
 # The queue kernels: profiles/queue_kernel_learned_sweep_4096x512x128.md and
 # profiles/queue_kernel_sweep_4096x512x128.md (4096 series each).
 NCU_TRAFFIC_PER_SERIES = {("plain", "sort"): 1646.202e6 / 4096, ("learned", "sort"): 1646.202e6 / 4096,
-                          ("learned", "queue"): 2426.104e6 / 4096, ("plain", "queue"): 2392.948e6 / 4096}
+                          ("learned", "queue"): 2387.792e6 / 4096, ("plain", "queue"): 2356.628e6 / 4096}
 STAGES = ["upload", "sort", "proposals", "queue", "collect"]
 
 
@@ -99,7 +99,7 @@ class ClockSampler:
     Any NVML client attached to the GPU (this sampler, an idle nvidia-smi, or one NVML handle in
     the process) slows the segmentation by about 2.3% on B300, whatever it queries and however
     often, so every device-timed arm that a ratio compares runs with a sampler of its own."""
-    FIELDS =("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
