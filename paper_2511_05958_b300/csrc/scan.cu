@@ -936,8 +936,9 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
     uint32_t gk = 0;  // g of split kb + lane
     int kb = A;
     // The results of split k - 1 (block sum, relative max and min, a C below the block) are
-    // finished in iteration k, while its first loads are in flight: a warp scan of the block
-    // sums, the block's true max and min, the warp maximum of the moduli, and the argmax.
+    // finished in iteration k, inside the first group of split k's evaluation: a warp scan of
+    // the block sums, the block's true max and min, the warp maximum of the moduli, and the
+    // argmax (split_g and finish do the same for the last split of a range).
     uint32_t p_blk = 0, p_h0 = 0;
     int32_t p_mx = 0, p_mn = 0;
     auto split_g = [&]() {
@@ -965,6 +966,60 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
             }
             kb = kp + 1;
         }
+    };
+    // evaluate split k with the finish of split kp (= k - 1) interleaved into its first group of
+    // quads, which every block has, so that the scan's shuffles overlap the evaluation
+    auto evaluate_fin = [&](int k, int kp, int kend) {
+        const uint32_t pb = p_blk, ph = p_h0;
+        const int32_t pmx = p_mx, pmn = p_mn;
+        const uint32_t a = (uint32_t)(k - lo), na = 0u - a;
+        const uint32_t h0 = a * Cb;
+        uint32_t hc = h0;
+        int32_t mx = INT_MIN, mn = INT_MAX;
+        uint4 q0 = lq[0], q1 = lq[1];
+        uint32_t incl = pb;
+        {
+            const uint4 n0 = lq[2], n1 = lq[3];
+            uint32_t y = __shfl_up_sync(kFull, incl, 1);
+            if (lane >= 1) incl += y;
+            sweep_eval4(q0, Cr[0], Cr[1], Cr[2], Cr[3], na, hc, mx, mn);
+            y = __shfl_up_sync(kFull, incl, 2);
+            if (lane >= 2) incl += y;
+            sweep_eval4(q1, Cr[4], Cr[5], Cr[6], Cr[7], na, hc, mx, mn);
+            y = __shfl_up_sync(kFull, incl, 4);
+            if (lane >= 4) incl += y;
+            y = __shfl_up_sync(kFull, incl, 8);
+            if (lane >= 8) incl += y;
+            y = __shfl_up_sync(kFull, incl, 16);
+            if (lane >= 16) incl += y;
+            q0 = n0;
+            q1 = n1;
+        }
+        const uint32_t vs = (incl - pb) - ph;  // split kp: v at the run before the block
+        const int32_t bmax = (int32_t)(vs + (uint32_t)pmx), bmin = (int32_t)(vs + (uint32_t)pmn);
+        const uint32_t g = __reduce_max_sync(kFull, (uint32_t)max(bmax, -bmin));
+#pragma unroll
+        for (int gg = 1; gg < kSweepMaxR / 8; gg++) {
+            if (2 * gg >= nq) break;
+            const uint4 n0 = lq[2 * gg + 2], n1 = lq[2 * gg + 3];
+            sweep_eval4(q0, Cr[8 * gg], Cr[8 * gg + 1], Cr[8 * gg + 2], Cr[8 * gg + 3], na, hc, mx, mn);
+            sweep_eval4(q1, Cr[8 * gg + 4], Cr[8 * gg + 5], Cr[8 * gg + 6], Cr[8 * gg + 7], na, hc, mx, mn);
+            q0 = n0;
+            q1 = n1;
+        }
+        if (lane == kp - kb) gk = g;
+        if (kp - kb == 31 || kp == kend) {
+            const int kk = kb + lane;
+            if (kk <= kp && better(kk, (uint64_t)gk, bk, bg, lo, hi)) {
+                bk = kk;
+                bg = gk;
+            }
+            kb = kp + 1;
+        }
+        p_blk = hc - h0;
+        p_h0 = h0;
+        p_mx = mx;
+        p_mn = mn;
     };
     // the values of split k into p_blk, p_h0, p_mx, p_mn (l holds the left counts of split k)
     auto evaluate = [&](int k) {
@@ -1091,9 +1146,8 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
             nxt = nxt2;
             sweep_load_step<VEC>(rk, min(k + 2, Bi), m, lane, nxt2);  // past Bi: a step of the segment, unused
             __syncwarp();
-            finish(k - 1, Bi);  // at k = Ai it records nothing (no lane has split kb - 1)
             nev++;
-            evaluate(k);
+            evaluate_fin(k, k - 1, Bi);  // at k = Ai it records nothing (no lane has split kb - 1)
             // every lane has read l for split k: step k's samples move left now (reductions the warp
             // does not wait for)
             __syncwarp();
