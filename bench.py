@@ -50,7 +50,7 @@ WORKLOADS = {
     "plain": (2, 1, 1024, False, "plain full segmentation, 1024 series x T=512 x m=128 uint32"),
     "uneven": (3, 2, 16384, False, "plain full segmentation, 16384 uneven series, T 32..4096, m 8..256"),
 }
-LAUNCHES = {False: 4, True: 8}  # our kernels per call (plain / learned)
+LAUNCHES = {False: 4, True: 9}  # our kernels per call (plain / learned: two gated queue launches)
 RECIPES = {2: "synth recipe 2 (T=512, m=128, levels 35/300/800/1100, 0.5% outliers)",
            3: "synth recipe 3 (T 32..4096, m 8..256, 0-4 level ratios 1.01..30, Pareto tails)"}
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch, per series, from the ncu

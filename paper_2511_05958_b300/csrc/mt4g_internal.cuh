@@ -119,6 +119,8 @@ struct QueueHeader {
 
 enum RunMode : int32_t { kRunScan = 0, kRunSegment = 1, kRunLearned = 2 };
 
+constexpr int32_t kGateNone = 0, kGateAllSwept = 1, kGateSomeUnswept = 2;
+
 struct RunParams {
     const SeriesDesc *desc;
     const uint16_t *lab;   // sorted labels (labA)
@@ -156,6 +158,9 @@ struct RunParams {
     int32_t win_only;           // 1: learned calls scan swept series only at their window splits
                                 //    (MT4G_OPT_LEARNED_WINDOWS)
     int32_t top_parts;          // parts of a top-level run-sweep segment (planned on the host)
+    int32_t gate;               // kGateNone, or which of a learned call's two queue launches works:
+                                // kGateAllSwept (every series swept: the plain kernel) or
+                                // kGateSomeUnswept (the learned kernel), read from q->unswept
 };
 
 // Number of slices of a segment of H steps (0 if it cannot be split).

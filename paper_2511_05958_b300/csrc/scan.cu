@@ -795,7 +795,9 @@ __device__ __forceinline__ bool window_interval(const RunParams &P, int series, 
     return true;
 }
 
-template <bool VEC, int WALK>
+// FUSE: the previous split's scan inside the next split's evaluation (evaluate_fin); 1.6% faster
+// in the plain kernels, 0.6% slower in the learned ones, whose routing code leaves less room.
+template <bool VEC, int WALK, bool FUSE>
 __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int hi, int A, int B, SweepStage &ss,
                            int &bk, uint64_t &bg, int &nonempty, int &nev, bool win = false, int series = 0) {
     const int lane = threadIdx.x & 31;
@@ -1147,7 +1149,12 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
             sweep_load_step<VEC>(rk, min(k + 2, Bi), m, lane, nxt2);  // past Bi: a step of the segment, unused
             __syncwarp();
             nev++;
-            evaluate_fin(k, k - 1, Bi);  // at k = Ai it records nothing (no lane has split kb - 1)
+            if constexpr (FUSE) {
+                evaluate_fin(k, k - 1, Bi);  // at k = Ai it records nothing (no lane has split kb - 1)
+            } else {
+                finish(k - 1, Bi);  // at k = Ai it records nothing (no lane has split kb - 1)
+                evaluate(k);
+            }
             // every lane has read l for split k: step k's samples move left now (reductions the warp
             // does not wait for)
             __syncwarp();
@@ -1511,6 +1518,10 @@ __device__ void slice_best(const RunParams &P, const SeriesDesc &d, int lo, int 
 template <bool LEARNED, bool SWEEP, int WALK = kWalkAll>
 __global__ void __launch_bounds__(SWEEP ? kSweepThreads : kScanThreads, SWEEP ? 8 : 4)
     queue_kernel(RunParams P, uint32_t epoch) {
+    if (P.gate != kGateNone) {  // one of a learned call's two launches: the sort's count decides which
+        const unsigned long long unswept = *(volatile const unsigned long long *)&P.q->unswept;
+        if ((P.gate == kGateAllSwept) != (unswept == 0)) return;
+    }
     using Smem = typename std::conditional<SWEEP, WarpSmem, WarpStage>::type;
     __shared__ Smem s_stage[(SWEEP ? kSweepThreads : kScanThreads) / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1595,9 +1606,11 @@ __global__ void __launch_bounds__(SWEEP ? kSweepThreads : kScanThreads, SWEEP ? 
                         bk = kNoK;  // no window split in this part's range
                         bg = 0;
                     } else if (vec) {
-                        sweep_best<true, WALK>(P, d, lo, hi, k0, it.klim, ss, bk, bg, nonempty, nev, win, it.series);
+                        sweep_best<true, WALK, !LEARNED>(P, d, lo, hi, k0, it.klim, ss, bk, bg, nonempty, nev, win,
+                                                         it.series);
                     } else {
-                        sweep_best<false, WALK>(P, d, lo, hi, k0, it.klim, ss, bk, bg, nonempty, nev, win, it.series);
+                        sweep_best<false, WALK, !LEARNED>(P, d, lo, hi, k0, it.klim, ss, bk, bg, nonempty, nev, win,
+                                                          it.series);
                     }
                     my_evals += (unsigned long long)nev * (unsigned long long)nonempty;
                     my_swept += it.chunk == 0;
@@ -1804,10 +1817,22 @@ int queue_grid_sweep(int device) {
 cudaError_t launch_queue_run(const RunParams &P, int grid, uint32_t epoch, cudaStream_t st) {
     if (P.mode == kRunLearned && P.rk && P.win_only)
         queue_kernel<true, true, kWalkWindows><<<grid, kSweepThreads, 0, st>>>(P, epoch);
-    else if (P.mode == kRunLearned && P.rk && P.sweep_skip)
-        queue_kernel<true, true, kWalkSkip><<<grid, kSweepThreads, 0, st>>>(P, epoch);
-    else if (P.mode == kRunLearned && P.rk)
-        queue_kernel<true, true><<<grid, kSweepThreads, 0, st>>>(P, epoch);
+    else if (P.mode == kRunLearned && P.rk) {
+        // A learned call whose every series the sweep takes has no learned work left (each series
+        // falls back to the full scan, and push_segment then pushes plain items only), so the
+        // plain instantiation, lighter by the learned routing, gives the same answers.  Both are
+        // launched; each reads the sort's count of unswept series first, and one of them works.
+        RunParams Pa = P, Pl = P;
+        Pa.gate = kGateAllSwept;
+        Pl.gate = kGateSomeUnswept;
+        if (P.sweep_skip) {
+            queue_kernel<false, true, kWalkSkip><<<grid, kSweepThreads, 0, st>>>(Pa, epoch);
+            queue_kernel<true, true, kWalkSkip><<<grid, kSweepThreads, 0, st>>>(Pl, epoch);
+        } else {
+            queue_kernel<false, true><<<grid, kSweepThreads, 0, st>>>(Pa, epoch);
+            queue_kernel<true, true><<<grid, kSweepThreads, 0, st>>>(Pl, epoch);
+        }
+    }
     else if (P.mode == kRunLearned)
         queue_kernel<true, false><<<grid, kScanThreads, 0, st>>>(P, epoch);
     else if (P.rk && P.sweep_skip)
