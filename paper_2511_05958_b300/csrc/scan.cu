@@ -591,9 +591,10 @@ __device__ __forceinline__ void warp_best(int &bk, uint64_t &bg, int lo, int hi)
 // 32-bit integer.
 //
 // Layout: the l of lane L's block sits at words [L Rs, L Rs + R) of the stage, Rs = R + 4; a
-// lane reads its block four runs at a time (16-byte loads), and with Rs = 4 mod 8 the eight lanes of a quarter warp start on eight different
-// four-bank groups, so the loads are free of bank conflicts.  Each lane keeps its block's C
-// in registers (they do not change during a segment's sweep).
+// lane reads its block four runs at a time (16-byte loads), and with Rs = 4 mod 8 the eight
+// lanes of a quarter warp start on eight different four-bank groups, so the loads are free of
+// bank conflicts.  Each lane keeps its block's C in registers (they do not change during a
+// segment's sweep).
 constexpr int kSweepMaxR = 48;                       // ceil(kSweepMaxRuns / 32), a multiple of 8
 constexpr int kSweepLWords = 32 * (kSweepMaxR + 4);  // largest padded layout
 // The evaluation loads a lane's next two quads before it knows whether its block has them: the
