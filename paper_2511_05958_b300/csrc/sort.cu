@@ -334,7 +334,25 @@ __device__ bool count_values(SortSmem &sm, const uint32_t *__restrict__ in, int3
     // is a multiple of 4 samples, and the label arrays are 256-byte aligned); else 2-byte stores
     uint16_t *o = rko + vs.head;
     const bool st8 = ((uintptr_t)o & 7u) == 0;  // the same for every thread
-    for (int b0 = 0; b0 < vs.nvec; b0 += kSortThreads * kCountVec) {
+    int b0 = 0;
+    if (st8) {  // whole rounds: no per-sample tests
+        for (; b0 + kSortThreads * kCountVec <= vs.nvec; b0 += kSortThreads * kCountVec) {
+            uint4 x[kCountVec];
+#pragma unroll
+            for (int it = 0; it < kCountVec; it++) x[it] = ld_hint(v4 + b0 + it * kSortThreads + tid, pol_first());
+#pragma unroll
+            for (int it = 0; it < kCountVec; it++) {
+                count_one(cnt, x[it].x, base, true, out, vmin, vmax);
+                count_one(cnt, x[it].y, base, true, out, vmin, vmax);
+                count_one(cnt, x[it].z, base, true, out, vmin, vmax);
+                count_one(cnt, x[it].w, base, true, out, vmin, vmax);
+                st_hint(reinterpret_cast<uint2 *>(o) + b0 + it * kSortThreads + tid,
+                        make_uint2(((x[it].x - base) & 0xffffu) | ((x[it].y - base) << 16),
+                                   ((x[it].z - base) & 0xffffu) | ((x[it].w - base) << 16)), pol_last());
+            }
+        }
+    }
+    for (; b0 < vs.nvec; b0 += kSortThreads * kCountVec) {
         uint4 x[kCountVec];
 #pragma unroll
         for (int it = 0; it < kCountVec; it++) {
@@ -448,7 +466,19 @@ __device__ bool count_runs(SortSmem &sm, const uint32_t *__restrict__ in, int32_
     uint16_t *o = rko + vs.head;
     if (((uintptr_t)o & 7u) == 0) {  // the same for every thread
         uint2 *o8 = reinterpret_cast<uint2 *>(o);
-        for (int b0 = 0; b0 < vs.nvec; b0 += kSortThreads * kCountVec) {
+        int b0 = 0;
+        for (; b0 + kSortThreads * 8 <= vs.nvec; b0 += kSortThreads * 8) {  // whole rounds: no tests
+            uint2 x[8];
+#pragma unroll
+            for (int it = 0; it < 8; it++) x[it] = o8[b0 + it * kSortThreads + tid];
+#pragma unroll
+            for (int it = 0; it < 8; it++) {
+                const uint32_t r0 = cnt[x[it].x & 0xffffu], r1 = cnt[x[it].x >> 16];
+                const uint32_t r2 = cnt[x[it].y & 0xffffu], r3 = cnt[x[it].y >> 16];
+                st_hint(o8 + b0 + it * kSortThreads + tid, make_uint2(r0 | (r1 << 16), r2 | (r3 << 16)), pol_first());
+            }
+        }
+        for (; b0 < vs.nvec; b0 += kSortThreads * kCountVec) {
             uint2 x[kCountVec];
 #pragma unroll
             for (int it = 0; it < kCountVec; it++) {
