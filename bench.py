@@ -60,7 +60,7 @@ RECIPES = {2: "synth recipe 2 (T=512, m=128, levels 35/300/800/1100, 0.5% outlie
 # are now appear here; the others report null.
 # The queue: profiles/queue_kernel_sweep_4096x512x128.md (4096 series; learned calls on this
 # distribution run the same plain instantiation as plain calls).
-NCU_TRAFFIC_PER_SERIES = {("plain", "sort"): 1646.202e6 / 4096, ("learned", "sort"): 1646.202e6 / 4096,
+NCU_TRAFFIC_PER_SERIES = {("plain", "sort"): 1668.576e6 / 4096, ("learned", "sort"): 1668.576e6 / 4096,
                           ("learned", "queue"): 2358.536e6 / 4096, ("plain", "queue"): 2358.536e6 / 4096}
 STAGES = ["upload", "sort", "proposals", "queue", "collect"]
 
