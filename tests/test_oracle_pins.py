@@ -354,6 +354,29 @@ def test_reduce_series_values():
     assert np.allclose(S, [math.sqrt(5), 0.0, math.sqrt(65)], rtol=0, atol=1e-15)
 
 
+def test_reduce_series_pythagorean_closed_forms(rng):
+    """Eq. 2 on steps whose offsets from the series minimum form Pythagorean quadruples and
+    quintuples: the root is an exact integer, whatever the order of the FP64 sum (every partial
+    sum is an integer below 2^53).  Reordering a step's samples and scaling every offset by an
+    integer c (S scales by c exactly here) change nothing else."""
+    quads = [(1, 2, 2, 3), (2, 3, 6, 7), (1, 4, 8, 9), (4, 4, 7, 9), (2, 6, 9, 11), (6, 6, 7, 11),
+             (1, 12, 12, 17), (8, 9, 12, 17), (12, 16, 21, 29), (1, 2, 4, 10, 11)]
+    base = 1000
+    for c in (1, 7, 4096):
+        rows, want = [], []
+        for q in quads:
+            *parts, root = q
+            row = [base] + [base + c * v for v in parts]
+            row += [base] * (5 - len(row))
+            rows.append(row)
+            want.append(c * root)
+        x = np.array(rows, np.uint32)
+        S = oracle.reduce_series(x)
+        assert [float(v) for v in S] == [float(w) for w in want]
+        xp = np.array([rng.permutation(r) for r in rows], np.uint32)
+        assert np.array_equal(oracle.reduce_series(xp), S)
+
+
 def test_single_series_64x32_golden_fixture():
     """The stored fixture (written by tests/golden/make_golden.py from the oracle) still holds."""
     import json
