@@ -16,6 +16,8 @@
 // in value order to labA and the start of every run of equal values.  For series with at
 // most kSweepMaxRuns distinct values a final read writes every sample's run index, in input
 // order, to labB (the scan's run sweep reads it step by step).
+#include <type_traits>
+
 #include "mt4g_internal.cuh"
 
 namespace mt4g {
@@ -137,8 +139,11 @@ __device__ void lsd_passes(SortSmem &sm, int passes, const uint32_t *__restrict_
         scan256(sm.hist, sm.base, sm.tmp);
         if (tid < 256) sm.hist2[tid] = 0;
         __syncthreads();
-        for (int tb = 0; tb < N; tb += kSortTile) {
-            const int tn = min(kSortTile, N - tb);
+        // one tile; FULL: the tile lies wholly inside the series (every tile but the last), so
+        // no sample is tested against N
+        auto tile = [&](const int tb, auto full_c) {
+            constexpr bool FULL = decltype(full_c)::value;
+            const int tn = FULL ? kSortTile : min(kSortTile, N - tb);
             for (int j = lane; j < 256; j += 32) sm.wc[warp][j] = 0;
             __syncwarp();
             uint32_t key[kSortItems], rk[kSortItems];
@@ -149,7 +154,7 @@ __device__ void lsd_passes(SortSmem &sm, int passes, const uint32_t *__restrict_
                 const int e = tb + warp * (32 * kSortItems) + it * 32 + lane;
                 key[it] = 0;
                 lb[it] = 0;
-                if (e < N) {
+                if (FULL || e < N) {
                     if (p == 0) {
                         key[it] = __ldg(in + e);
                     } else {
@@ -165,7 +170,7 @@ __device__ void lsd_passes(SortSmem &sm, int passes, const uint32_t *__restrict_
 #pragma unroll
                 for (int it = 0; it < kSortItems; it++) {
                     const int e = tb + warp * (32 * kSortItems) + it * 32 + lane;
-                    const uint32_t ec = (uint32_t)min(e, N - 1);
+                    const uint32_t ec = FULL ? (uint32_t)e : (uint32_t)min(e, N - 1);
                     const uint32_t t = pow2 ? ec >> msh : div_step(ec, (uint32_t)m, inv_m);
                     if (COMP) key[it] = (key[it] << 16) | t;
                     lb[it] = (uint16_t)t;
@@ -174,8 +179,8 @@ __device__ void lsd_passes(SortSmem &sm, int passes, const uint32_t *__restrict_
 #pragma unroll
             for (int it = 0; it < kSortItems; it++) {
                 const int e = tb + warp * (32 * kSortItems) + it * 32 + lane;
-                const bool valid = e < N;
-                const unsigned vm = __ballot_sync(kFull, valid);
+                const bool valid = FULL || e < N;
+                const unsigned vm = FULL ? kFull : __ballot_sync(kFull, valid);
                 const uint32_t val = COMP ? key[it] >> 16 : key[it];
                 const uint32_t dg = (val >> shift) & 255u;
                 const unsigned peers = digit_peers(dg, vm);
@@ -213,7 +218,7 @@ __device__ void lsd_passes(SortSmem &sm, int passes, const uint32_t *__restrict_
 #pragma unroll
             for (int it = 0; it < kSortItems; it++) {
                 const int e = tb + warp * (32 * kSortItems) + it * 32 + lane;
-                if (e < N) {
+                if (FULL || e < N) {
                     const uint32_t val = COMP ? key[it] >> 16 : key[it];
                     const uint32_t dg = (val >> shift) & 255u;
                     const uint32_t local = sm.wc[warp][dg] + rk[it];
@@ -233,6 +238,12 @@ __device__ void lsd_passes(SortSmem &sm, int passes, const uint32_t *__restrict_
             __syncthreads();
             if (tid < 256) sm.base[tid] += sm.tcnt[tid];
             __syncthreads();
+        };
+        for (int tb = 0; tb < N; tb += kSortTile) {
+            if (tb + kSortTile <= N)
+                tile(tb, std::true_type{});
+            else
+                tile(tb, std::false_type{});
         }
         if (tid < 256) sm.hist[tid] = sm.hist2[tid];
         __syncthreads();
