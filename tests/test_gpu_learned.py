@@ -297,6 +297,42 @@ def test_learned_mode_equals_full_on_three_level_series(eng, seed):
     assert (np.abs(learned[1][4][sample] - op) <= 1e-12 * np.abs(op)).all()
 
 
+@pytest.mark.parametrize("mixed", [False, True])
+def test_learned_queue_launch_gate(eng, mixed):
+    """A learned call launches the plain and the learned queue instantiation; the sort's count of
+    series the sweep does not take decides which one works.  All swept (three-level series, at
+    most 1536 distinct values): the plain kernel, every series falls back to the full scan.
+    Mixed (plus series with thousands of distinct values): the learned kernel.  Either way the
+    answers are the oracle's and the plain call's."""
+    import oracle
+    rng = np.random.default_rng(77)
+    b0 = synth.generate(2, 41, 48)
+    series = [b0.series(s) for s in range(48)]
+    if mixed:
+        for _ in range(8):  # thousands of distinct values: the run sweep does not take them
+            T = int(rng.integers(40, 120))
+            lev = rng.integers(1000, 40000, size=(T, 1))
+            lev[T // 2:] += 5000
+            series.append((lev + rng.integers(0, 60000, size=(T, 64))).astype(np.uint32))
+    b = synth.from_arrays(series)
+    eng.cnn_init(5)
+    full = _segment(eng, b, mt4g.MODE_FULL)
+    learned = _segment(eng, b, mt4g.MODE_LEARNED)
+    unswept = eng.last_sweep()["unswept_series"]
+    assert (unswept > 0) == mixed
+    if not mixed:
+        assert (learned[1][5] == 1).all()  # every series swept: the full scan, by the plain kernel
+    rc_f, (cf, idf, nf, df, pf, _) = full
+    rc_l, (cl, idl, nl, dl, pl, _) = learned
+    assert rc_f == rc_l
+    for a, c in ((cf, cl), (idf, idl), (nf, nl), (df, dl), (pf, pl)):
+        assert np.array_equal(a, c)
+    _, ocnt, oidx, onum, oden, op = oracle.ks_segment(b.samples, b.offsets, b.steps, 1e-6, 1, 16, nthreads=8)
+    assert np.array_equal(cl, ocnt) and np.array_equal(idl, oidx)
+    assert np.array_equal(nl, onum) and np.array_equal(dl, oden)
+    assert (np.abs(pl - op) <= 1e-12 * np.abs(op)).all()
+
+
 def test_learned_mode_fallback_threshold(eng):
     b = synth.generate(2, 31, 64)
     eng.cnn_init(7)
