@@ -939,9 +939,10 @@ __device__ void sweep_best(const RunParams &P, const SeriesDesc &d, int lo, int 
     uint32_t gk = 0;  // g of split kb + lane
     int kb = A;
     // The results of split k - 1 (block sum, relative max and min, a C below the block) are
-    // finished in iteration k, inside the first group of split k's evaluation: a warp scan of
-    // the block sums, the block's true max and min, the warp maximum of the moduli, and the
-    // argmax (split_g and finish do the same for the last split of a range).
+    // finished in iteration k: a warp scan of the block sums, the block's true max and min, the
+    // warp maximum of the moduli, and the argmax.  With FUSE (the plain kernels) this runs inside
+    // the first group of split k's evaluation (evaluate_fin), else just before it (finish); the
+    // last split of a range is finished after the loop.
     uint32_t p_blk = 0, p_h0 = 0;
     int32_t p_mx = 0, p_mn = 0;
     auto split_g = [&]() {
